@@ -1,0 +1,239 @@
+"""Seeded synthetic workloads shaped like the paper's scenarios.
+
+This module only makes inputs: the model kind and its parameter vector, the
+initial states x_0 and the observation sequences z_{1:T}. It holds none of the
+estimator's arithmetic (no SVGD, no bandwidth, no recursion). To simulate the
+ground-truth trajectories it restates each scenario's forward map in numpy
+(a copy of the model equations used only to draw observations).
+
+Workloads (sizes can be shrunk for tests; the default sizes are the full ones):
+  ngm1d       1-D nonstationary growth model, sign-ambiguous z = x^2/20 + w,
+              N=32, L=50, T=50, one sequence.                       (Section V-A form)
+  range_cv    2-D range-only localisation, constant velocity d=4, three beacons
+              in [0,100]^2, beacons 2 and 3 silent for steps 60..120,
+              N=256, L=30, T=200, B=1024.                           (Section V-C form)
+  clutter_cv  unknown data association: 10 points per step, one true (20%
+              missed) and clutter uniform in [-50,50]^2, N=512, L=30,
+              T ~ U[50,400], B=4096.                                 (Section V-B form)
+  planar_arm  7-link planar chain (links 0.3 m), 14-D state, 2-D end effector,
+              N=1024, L=50, T=100, B=256.                           (Section V-D form)
+  linear_gauss constant velocity with direct position measurements: the
+              linear-Gaussian case used by the smoother check.
+Parameter-vector layouts are the ones documented in include/smap.h.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+BASE_SEED = 20231208
+
+MODEL_NGM1D, MODEL_RANGE_CV2D, MODEL_CLUTTER_CV2D, MODEL_PLANAR_ARM, MODEL_LINEAR_GAUSS = 1, 2, 3, 4, 5
+BW_MEDIAN_ITER, BW_MEDIAN_STEP, BW_FIXED = 0, 1, 2
+PRIOR_MIXTURE, PRIOR_MEANGRAD = 0, 1
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    kind: int
+    params: np.ndarray        # float64 parameter vector (layout per model)
+    d: int
+    dy: int
+    N: int                    # particles (maximum over the batch)
+    L: int                    # SVGD iterations per step
+    step: float               # SVGD step size epsilon
+    bw_rule: int
+    bw_value: float
+    prior: int
+    seed: int                 # estimator RNG seed (particle initialisation)
+    x0: np.ndarray            # [B][d] float64, the known initial state
+    y: np.ndarray             # [B][maxT][dy] float32 observations (NaN = not observed)
+    T: np.ndarray             # [B] int32 sequence lengths
+    Nseq: np.ndarray          # [B] int32 particles per sequence
+    truth: np.ndarray         # [B][maxT+1][d] float64 simulated states
+
+    @property
+    def B(self) -> int:
+        return int(self.x0.shape[0])
+
+    @property
+    def maxT(self) -> int:
+        return int(self.y.shape[1])
+
+    def pair_evals(self) -> float:
+        """RBF pair evaluations of a whole run: sum_s N_s^2 L T_s."""
+        return float(np.sum(self.Nseq.astype(np.float64) ** 2 * self.L * self.T))
+
+    def particle_updates(self) -> float:
+        """SVGD particle updates of a whole run: sum_s N_s L T_s."""
+        return float(np.sum(self.Nseq.astype(np.float64) * self.L * self.T))
+
+    def subset(self, idx) -> "Workload":
+        idx = np.asarray(idx)
+        T = self.T[idx]
+        mt = int(T.max())
+        return dataclasses.replace(
+            self, x0=self.x0[idx].copy(), y=np.ascontiguousarray(self.y[idx, :mt]),
+            T=T.copy(), Nseq=self.Nseq[idx].copy(), truth=self.truth[idx, : mt + 1].copy())
+
+
+def _rng(*key):
+    return np.random.default_rng([BASE_SEED, *[int(k) for k in key]])
+
+
+# ---------------------------------------------------------------- ngm1d ----
+def ngm1d_params(paper_constants: bool = False) -> np.ndarray:
+    if paper_constants:   # Section V-A: 0.9x + 10x/(1+x^2) + 8cos(1.2(t-1)), v~N(0,5), r~N(0,16)
+        return np.array([0.9, 10.0, 8.0, 1.2, -1.0, 5.0, 16.0, 0.05])
+    return np.array([0.5, 25.0, 8.0, 1.2, 0.0, 10.0, 1.0, 0.05])
+
+
+def make_ngm1d(B=1, T=50, N=32, L=50, step=0.05, seed=1, paper_constants=False,
+               bw_value=1.0, prior=PRIOR_MIXTURE) -> Workload:
+    p = ngm1d_params(paper_constants)
+    a, b, c, om, toff, q, r, hc = p
+    x0 = np.zeros((B, 1)); y = np.zeros((B, T, 1), np.float32); truth = np.zeros((B, T + 1, 1))
+    for s in range(B):
+        g = _rng(1, s)
+        x = g.normal(0.0, np.sqrt(5.0))
+        x0[s, 0] = x
+        truth[s, 0, 0] = x
+        for t in range(1, T + 1):
+            x = a * x + b * x / (1 + x * x) + c * np.cos(om * (t + toff)) + g.normal(0, np.sqrt(q))
+            truth[s, t, 0] = x
+            y[s, t - 1, 0] = hc * x * x + g.normal(0, np.sqrt(r))
+    return Workload("ngm1d", MODEL_NGM1D, p, 1, 1, N, L, step, BW_MEDIAN_ITER, bw_value, prior,
+                    seed, x0, y, np.full(B, T, np.int32), np.full(B, N, np.int32), truth)
+
+
+# ------------------------------------------------------------- range_cv ----
+def range_params(beacons, dt=0.1, q=0.01, r=0.25) -> np.ndarray:
+    beacons = np.asarray(beacons, np.float64)
+    return np.concatenate([[dt, q, q, q, q, r, len(beacons)], beacons.ravel()])
+
+
+def _cv_step(x, dt, g, q):
+    f = np.array([x[0] + dt * x[2], x[1] + dt * x[3], x[2], x[3]])
+    return f + g.normal(0.0, np.sqrt(q), 4)
+
+
+def make_range_cv(B=1024, T=200, N=256, L=30, step=0.005, seed=2, dropout=(60, 120),
+                  bw_value=1.0, prior=PRIOR_MIXTURE) -> Workload:
+    beacons = _rng(2, 999_999).uniform(0.0, 100.0, (3, 2))
+    p = range_params(beacons)
+    dt, q, r = p[0], p[1], p[5]
+    x0 = np.zeros((B, 4)); y = np.zeros((B, T, 3), np.float32); truth = np.zeros((B, T + 1, 4))
+    for s in range(B):
+        g = _rng(2, s)
+        x = np.concatenate([g.uniform(25.0, 75.0, 2), g.normal(0.0, 1.0, 2)])
+        x0[s] = x
+        truth[s, 0] = x
+        for t in range(1, T + 1):
+            x = _cv_step(x, dt, g, q)
+            truth[s, t] = x
+            rho = np.hypot(x[0] - beacons[:, 0], x[1] - beacons[:, 1])
+            z = rho + g.normal(0.0, np.sqrt(r), 3)
+            if dropout is not None and dropout[0] <= t <= dropout[1]:
+                z[1:] = np.nan
+            y[s, t - 1] = z
+    return Workload("range_cv", MODEL_RANGE_CV2D, p, 4, 3, N, L, step, BW_MEDIAN_ITER, bw_value,
+                    prior, seed, x0, y, np.full(B, T, np.int32), np.full(B, N, np.int32), truth)
+
+
+# ----------------------------------------------------------- clutter_cv ----
+def clutter_params(dt=0.1, q=0.01, r=0.5, M=10, beta=0.2, area=100.0 * 100.0) -> np.ndarray:
+    return np.array([dt, q, q, q, q, r, M, beta, area])
+
+
+def make_clutter_cv(B=4096, Tmin=50, Tmax=400, N=512, L=30, step=0.005, seed=3, M=10,
+                    p_miss=0.2, bw_value=1.0, prior=PRIOR_MIXTURE, uneven_N=None) -> Workload:
+    p = clutter_params(M=M)
+    dt, q, r = p[0], p[1], p[5]
+    lengths = _rng(3, 888_888).integers(Tmin, Tmax + 1, B).astype(np.int32)
+    maxT = int(lengths.max())
+    x0 = np.zeros((B, 4)); y = np.full((B, maxT, 2 * M), np.nan, np.float32)
+    truth = np.full((B, maxT + 1, 4), np.nan)
+    for s in range(B):
+        g = _rng(3, s)
+        x = np.concatenate([g.uniform(-20.0, 20.0, 2), g.normal(0.0, 1.0, 2)])
+        x0[s] = x
+        truth[s, 0] = x
+        for t in range(1, int(lengths[s]) + 1):
+            x = _cv_step(x, dt, g, q)
+            truth[s, t] = x
+            pts = g.uniform(-50.0, 50.0, (M, 2))
+            if g.uniform() >= p_miss:
+                pts[g.integers(0, M)] = x[:2] + g.normal(0.0, np.sqrt(r), 2)
+            y[s, t - 1] = pts.ravel()
+    Nseq = np.full(B, N, np.int32)
+    if uneven_N is not None:
+        Nseq = _rng(3, 777_777).integers(uneven_N[0], uneven_N[1] + 1, B).astype(np.int32)
+    return Workload("clutter_cv", MODEL_CLUTTER_CV2D, p, 4, 2 * M, int(Nseq.max()), L, step,
+                    BW_MEDIAN_ITER, bw_value, prior, seed, x0, y, lengths, Nseq, truth)
+
+
+# ----------------------------------------------------------- planar_arm ----
+def arm_params(nl=7, dt=0.02, r=1e-4, qp=1.0, qv=0.01, link=0.3) -> np.ndarray:
+    qa = qp * dt * dt
+    return np.concatenate([[dt, nl, r], [qa] * nl, [qv] * nl, [link] * nl])
+
+
+def _arm_fk(qang, lengths):
+    th = np.cumsum(qang)
+    return np.array([np.sum(lengths * np.cos(th)), np.sum(lengths * np.sin(th))])
+
+
+def make_planar_arm(B=256, T=100, N=1024, L=50, step=1e-5, seed=4, nl=7, bw_value=1.0,
+                    prior=PRIOR_MIXTURE) -> Workload:
+    p = arm_params(nl=nl)
+    dt, r = p[0], p[2]
+    qv = p[3: 3 + 2 * nl]
+    lengths = p[3 + 2 * nl:]
+    d = 2 * nl
+    x0 = np.zeros((B, d)); y = np.zeros((B, T, 2), np.float32); truth = np.zeros((B, T + 1, d))
+    for s in range(B):
+        g = _rng(4, s)
+        x = np.concatenate([g.uniform(-0.5, 0.5, nl), np.zeros(nl)])
+        x0[s] = x
+        truth[s, 0] = x
+        for t in range(1, T + 1):
+            f = np.concatenate([x[:nl] + dt * x[nl:], x[nl:]])
+            x = f + g.normal(0.0, 1.0, d) * np.sqrt(qv)
+            truth[s, t] = x
+            y[s, t - 1] = _arm_fk(x[:nl], lengths) + g.normal(0.0, np.sqrt(r), 2)
+    return Workload("planar_arm", MODEL_PLANAR_ARM, p, d, 2, N, L, step, BW_MEDIAN_ITER, bw_value,
+                    prior, seed, x0, y, np.full(B, T, np.int32), np.full(B, N, np.int32), truth)
+
+
+# --------------------------------------------------------- linear_gauss ----
+def linear_params(dt=0.1, q=0.01, r=0.05) -> np.ndarray:
+    return np.array([dt, q, q, q, q, r])
+
+
+def make_linear_gauss(B=1, T=20, N=64, L=100, step=0.002, seed=5, q=0.01, r=0.05,
+                      bw_value=1.0, prior=PRIOR_MIXTURE) -> Workload:
+    p = linear_params(q=q, r=r)
+    dt = p[0]
+    x0 = np.zeros((B, 4)); y = np.zeros((B, T, 2), np.float32); truth = np.zeros((B, T + 1, 4))
+    for s in range(B):
+        g = _rng(5, s)
+        x = np.concatenate([g.uniform(-5.0, 5.0, 2), g.normal(0.0, 1.0, 2)])
+        x0[s] = x
+        truth[s, 0] = x
+        for t in range(1, T + 1):
+            x = _cv_step(x, dt, g, q)
+            truth[s, t] = x
+            y[s, t - 1] = x[:2] + g.normal(0.0, np.sqrt(r), 2)
+    return Workload("linear_gauss", MODEL_LINEAR_GAUSS, p, 4, 2, N, L, step, BW_MEDIAN_ITER,
+                    bw_value, prior, seed, x0, y, np.full(B, T, np.int32), np.full(B, N, np.int32),
+                    truth)
+
+
+FULL = {
+    "ngm1d": lambda: make_ngm1d(),
+    "range_cv": lambda: make_range_cv(),
+    "clutter_cv": lambda: make_clutter_cv(),
+    "planar_arm": lambda: make_planar_arm(),
+}
