@@ -1,0 +1,311 @@
+"""Benchmark of the Stein-MAP-Seq hot path on GB300.
+
+One "step" = one whole batched run of the workload through the C ABI
+(smap_run_batch): 1024 range-only sequences (d=4, 3 beacons), T=200 time
+steps, N=256 particles, L=30 SVGD iterations per time step, followed by the
+Viterbi recursion and backtracking. Metric: SVGD particle-updates/s
+(sum over sequences of N L T divided by the step time) and sequences/s.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl smap|reference]
+
+Under torchrun (N > 1) each rank runs its own 1024 sequences (weak scaling,
+no collective on the data path); rank 0 prints the JSON line with the time
+maxed over ranks. --impl reference times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2312_08684_gb300 import workloads as W  # noqa: E402
+
+WORKLOAD = dict(B=1024, T=200, N=256, L=30)
+METRIC = "SVGD particle-updates/s"
+UNIT = "particle-updates/s"
+
+
+def shard(rank: int, world: int, B: int):
+    """Sequence ids of one rank under weak scaling: rank r owns [r B, (r+1) B)."""
+    return list(range(rank * B, (rank + 1) * B))
+
+
+def make_workload(rank: int, B: int, T: int, N: int, L: int):
+    wl = W.make_range_cv(B=B, T=T, N=N, L=L, seed=2 + rank, first=rank * B)
+    return wl
+
+
+def algorithmic_ops(wl) -> float:
+    """FP32/SFU lane operations the method needs (per ordered pair-iteration
+    8d+8: RBF kernel and update 4d+1 + exp, mixture prior 3d+4 + exp, median
+    d+1; per ordered pair-step of the recursion screen 4d+4)."""
+    d = wl.d
+    n2 = wl.Nseq.astype(np.float64) ** 2
+    T = wl.T.astype(np.float64)
+    return float(np.sum(n2 * T * (wl.L * (8 * d + 8) + (4 * d + 4))))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def alu_peak_gops(sm_mhz: float, sms: int = 152) -> float:
+    """FP32 issue peak: 128 lanes per SM per clock (4 sub-partitions x 32)."""
+    return sms * 128 * sm_mhz * 1e6 / 1e9
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(wl_full, threads: int, T_sample: int):
+    """The FP64 oracle as it stands, one sequence per host thread, T_sample steps."""
+    from oracle import oracle as O
+    O.lib()
+    nseq = threads
+    sub = wl_full.subset(np.arange(nseq))
+    T = np.full(nseq, T_sample, np.int32)
+    t0 = time.perf_counter()
+    O.run_batch(sub.kind, sub.params, sub.N, sub.L, sub.step, sub.bw_rule, sub.bw_value, sub.prior,
+                sub.seed, np.arange(nseq), sub.x0, sub.y[:, :T_sample].astype(np.float64), T,
+                nthreads=threads)
+    dt = time.perf_counter() - t0
+    units = nseq * sub.N * sub.L * T_sample
+    return {"value": units / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{nseq} sequences x first {T_sample} of {wl_full.maxT} steps "
+                      f"(N={sub.N}, L={sub.L}), one sequence per host thread, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    threads = os.cpu_count() or 1
+    T_sample = 6
+    wl = make_workload(0, threads, T_sample, WORKLOAD["N"], WORKLOAD["L"])
+    from oracle import oracle as O
+    O.lib()
+
+    def one():
+        t0 = time.perf_counter()
+        O.run_batch(wl.kind, wl.params, wl.N, wl.L, wl.step, wl.bw_rule, wl.bw_value, wl.prior,
+                    wl.seed, np.arange(wl.B), wl.x0, wl.y.astype(np.float64), wl.T, nthreads=threads)
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        one()
+    times = [one() for _ in range(args.steps)]
+    ms = 1000.0 * float(np.mean(times))
+    units = float(wl.B * wl.N * wl.L * T_sample)
+    value = units / (ms / 1000.0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "range_cv: 2-D range-only CV (d=4, 3 beacons, beacons 2-3 silent "
+                               "for steps 60-120), N=256, L=30, T=200, B=1024 per GPU",
+                   "N": WORKLOAD["N"], "L": WORKLOAD["L"], "T": WORKLOAD["T"], "B": WORKLOAD["B"],
+                   "reference_step": f"{threads} sequences x {T_sample} steps on {threads} host threads"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{threads} sequences x first {T_sample} steps per bench step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="smap", choices=["smap", "reference"])
+    ap.add_argument("--B", type=int, default=WORKLOAD["B"])
+    ap.add_argument("--T", type=int, default=WORKLOAD["T"])
+    ap.add_argument("--N", type=int, default=WORKLOAD["N"])
+    ap.add_argument("--L", type=int, default=WORKLOAD["L"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2312_08684_gb300 import Estimator, _binding as abi
+
+    wl = make_workload(rank, args.B, args.T, args.N, args.L)
+    stream = torch.cuda.Stream()
+    est = Estimator.from_workload(wl, stream=stream)
+    y_dev = torch.from_numpy(wl.y).to(f"cuda:{local}")
+    path_dev = torch.empty((wl.B, wl.maxT + 1, wl.d), dtype=torch.float32, device=f"cuda:{local}")
+    J_dev = torch.empty(wl.B, dtype=torch.float64, device=f"cuda:{local}")
+    if args.autotune:
+        est.autotune(y_dev, sample=2 * 152, steps=3)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+
+    def device_step():
+        abi.smap_run_batch(est.h, y_dev, None, None, path_dev, J_dev)
+
+    for _ in range(max(args.warmup, 3)):
+        device_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = abi.smap_kernel_launches()
+    step_ms, kern_ms = [], []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()                       # L2 flush between timed steps (256 MB write)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            device_step()
+            ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        kern_ms.append(abi.smap_last_kernel_ms(est.h)[0])
+    torch.cuda.synchronize()
+    launches = abi.smap_kernel_launches() - launches0
+    clk = clocks.stop()
+    ms = float(np.mean(step_ms))
+    if dist:
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    units_rank = wl.particle_updates()
+    value = units_rank * world / (ms / 1000.0)
+
+    # end to end through the public call with host buffers (pinned), copies inside
+    y_pin = torch.from_numpy(wl.y).pin_memory()
+    path_pin = torch.empty((wl.B, wl.maxT + 1, wl.d), dtype=torch.float32).pin_memory()
+    J_pin = torch.empty(wl.B, dtype=torch.float64).pin_memory()
+    e2e_t = []
+    for k in range(max(2, min(args.steps, 3)) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        abi.smap_run_batch(est.h, y_pin, None, None, path_pin, J_pin)
+        if k:
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_s = float(np.mean(e2e_t))
+    if dist:
+        t = torch.tensor([e2e_s], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        est.close()
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    pk, src = peaks()
+    sm_for_peak = pk.get("sm_max_mhz", 2070.0)
+    peak = alu_peak_gops(sm_for_peak)
+    kms = float(np.mean(kern_ms))
+    achieved = algorithmic_ops(wl) / (kms / 1000.0) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        with open(tr_path) as f:
+            traffic = json.load(f).get("seq_kernel_bytes_per_launch")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "sequences_per_s": wl.B * world / (ms / 1000.0),
+        "config": {"workload": "range_cv: 2-D range-only CV (d=4, 3 beacons, beacons 2-3 silent for "
+                               "steps 60-120), N=256, L=30, T=200, B=1024 per GPU; FP32 particles, "
+                               "FP64 Viterbi scores",
+                   "N": wl.N, "L": wl.L, "T": wl.maxT, "B": wl.B, "parallelism": f"sequences x{world}",
+                   "l2": "flushed between timed steps (256 MB write)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "seq_kernel",
+                     "kernel_ms": kms,
+                     "peak_basis": f"152 SMs x 128 FP32 lanes x {sm_for_peak:.0f} MHz ({src} max clock)"},
+        "e2e": {"value": units_rank * world / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(wl.y.nbytes),
+                "d2h_bytes_per_step": int(path_pin.numel() * 4 + J_pin.numel() * 8)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, os.cpu_count() or 1, 30)
+    print(json.dumps(line), flush=True)
+    est.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,219 @@
+/*
+ * smap.h -- C ABI of the GB300 Stein-MAP-Seq library (libsmap.so).
+ *
+ * Stein-MAP-Seq (Seo & Kia, arXiv 2312.08684) estimates the MAP state sequence
+ * x_{0:T} of a state-space model from observations z_{1:T} (Section II,
+ * Eq. MAP_est). At every step t it moves N particles with L iterations of Stein
+ * variational gradient descent toward p(z_t, x_t | previous particle set)
+ * (Algorithm 1; directions Eq. SVGD_initial_newupdate for t = 1 and
+ * Eq. SVGD_newupdate for t >= 2), then runs one step of a Viterbi max-plus
+ * recursion over consecutive particle sets (Eq. forward_recursion); the MAP
+ * path is read back by backtracking (Section IV-B, Algorithm 2).
+ *
+ * Conventions that hold for every call:
+ *   - Every call returns an smap_status; nothing throws across the ABI.
+ *   - A handle owns all of its device memory (allocated in smap_create, freed in
+ *     smap_destroy). The caller owns every buffer it passes in.
+ *   - "on_device" = 1 means the data pointers of that call are device pointers
+ *     (e.g. torch.Tensor.data_ptr() of a CUDA tensor); 0 means host pointers.
+ *   - Work is queued on the handle's stream (smap_config.stream; NULL = the
+ *     legacy default stream). Calls that return results to host memory, and
+ *     smap_map_sequence / smap_run_batch / smap_viterbi, synchronise that stream
+ *     before returning.
+ *   - The first CUDA error puts the handle into a failed state: later calls
+ *     return SMAP_E_STATE. smap_last_error() gives the message.
+ *   - One handle is used by one host thread at a time.
+ *   - Arrays are dense, row-major, without padding; d = state dimension,
+ *     dy = observation dimension of the model (smap_dims).
+ *   - Particles are FP32; cumulative Viterbi scores phi_t and J are FP64.
+ */
+#ifndef SMAP_H
+#define SMAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SMAP_OK = 0,
+    SMAP_E_INVAL = 1,        /* bad argument (size, model parameters, null pointer) */
+    SMAP_E_NOMEM = 2,        /* device or host allocation failed */
+    SMAP_E_CUDA = 3,         /* a CUDA runtime call failed */
+    SMAP_E_STATE = 4,        /* handle already failed, or call out of order */
+    SMAP_E_TIMEOUT = 5,      /* a bounded device wait ran out */
+    SMAP_E_NONFINITE = 6,    /* a particle or observation became NaN/Inf */
+    SMAP_E_UNSUPPORTED = 7   /* valid request this build does not implement */
+} smap_status;
+
+/* Compiled-in scenario models. Parameter vectors (FP64), d and dy:
+ *  SMAP_MODEL_NGM1D        [a, b, c, omega, t_off, q, r, hcoef]        d=1, dy=1
+ *      x_t = a x + b x/(1+x^2) + c cos(omega (t + t_off)) + N(0, q)
+ *      z_t = hcoef x_t^2 + N(0, r)          (Section V-A form)
+ *  SMAP_MODEL_RANGE_CV2D   [dt, q0, q1, q2, q3, r, nb, b0x, b0y, ...]  d=4, dy=nb (1..8)
+ *      state (px, py, vx, vy), constant velocity with step dt, Q = diag(q0..q3);
+ *      z_l = ||(px,py) - b_l|| + N(0, r); a NaN entry of z means beacon l was
+ *      not heard at that step (Section V-C form)
+ *  SMAP_MODEL_CLUTTER_CV2D [dt, q0, q1, q2, q3, r, M, beta, area]      d=4, dy=2M (M 1..32)
+ *      constant velocity; z = M points; p(z|x) = (1-beta)(1/M) sum_m
+ *      N(z_m; (px,py), r I) + beta/area   (unknown association with outliers,
+ *      Section V-B form)
+ *  SMAP_MODEL_PLANAR_ARM   [dt, nl, r, q_0..q_{2nl-1}, len_0..len_{nl-1}] d=2nl, dy=2
+ *      state (angles, rates), angles += dt * rates; z = sum_l len_l (cos th_l,
+ *      sin th_l), th_l = sum_{m<=l} angle_m, noise N(0, r I) (Section V-D form;
+ *      this build compiles nl = 7)
+ *  SMAP_MODEL_LINEAR_GAUSS [dt, q0, q1, q2, q3, r]                     d=4, dy=2
+ *      constant velocity, z = (px, py) + N(0, r I)
+ */
+typedef enum {
+    SMAP_MODEL_NGM1D = 1,
+    SMAP_MODEL_RANGE_CV2D = 2,
+    SMAP_MODEL_CLUTTER_CV2D = 3,
+    SMAP_MODEL_PLANAR_ARM = 4,
+    SMAP_MODEL_LINEAR_GAUSS = 5
+} smap_model;
+
+/* Kernel bandwidth h of kappa(x,x') = exp(-||x-x'||^2 / h) (the RBF kernel of
+ * Section V, median heuristic of the Table Ex6 caption):
+ *   MEDIAN_ITER  h = bw_value * med / log N, med = median of the squared
+ *                pairwise distances (i < k; mean of the two middle values when
+ *                their count is even), recomputed every SVGD iteration;
+ *   MEDIAN_STEP  the same, computed at the first iteration of each step;
+ *   FIXED        h = bw_value.
+ * N = 1 or med = 0 gives h = 1. */
+typedef enum { SMAP_BW_MEDIAN_ITER = 0, SMAP_BW_MEDIAN_STEP = 1, SMAP_BW_FIXED = 2 } smap_bw_rule;
+
+/* Prior term of the direction of Eq. SVGD_newupdate:
+ *   MIXTURE   score of log (1/N) sum_j p(x | x_{t-1}^j) (responsibility-weighted)
+ *   MEANGRAD  mean over j of grad log p(x | x_{t-1}^j) = Q^-1 (mean_j f_j - x)
+ * They coincide when the previous set has one particle (t = 1). */
+typedef enum { SMAP_PRIOR_MIXTURE = 0, SMAP_PRIOR_MEANGRAD = 1 } smap_prior;
+
+typedef struct smap_handle smap_handle;
+
+typedef struct {
+    int model;              /* smap_model */
+    const double* params;   /* host, copied at create */
+    int n_params;
+    int N;                  /* particles per sequence (maximum if N varies), 1..4096 */
+    int L;                  /* SVGD iterations per step, >= 0 */
+    double step;            /* SVGD step size epsilon (Algorithm 1) */
+    int bw_rule;            /* smap_bw_rule */
+    double bw_value;        /* scale for the median rules, h for FIXED */
+    int prior;              /* smap_prior */
+    uint64_t seed;          /* key of the Philox-4x32-10 noise of the particle initialisation */
+    int batch;              /* number of independent sequences B >= 1 */
+    int max_T;              /* longest sequence the handle can hold */
+    const double* x0;       /* host [batch][d]: the known initial states x_0^true */
+    void* stream;           /* cudaStream_t (NULL = legacy default stream) */
+} smap_config;
+
+/* Validates cfg, allocates the handle's device buffers (particle history
+ * [B][max_T][N][d] FP32, backpointers [B][max_T][N] uint16, scores [B][N]
+ * FP64, work queue and scratch). No kernel runs. *out is NULL on failure. */
+smap_status smap_create(const smap_config* cfg, smap_handle** out);
+
+/* Frees everything the handle owns (synchronises its stream). NULL is a no-op. */
+void smap_destroy(smap_handle* h);
+
+/* d and dy of the handle's model. */
+smap_status smap_dims(const smap_handle* h, int* d, int* dy);
+
+/* Back to t = 0 for every sequence; x0 (host [B][d]) replaces the initial
+ * states when not NULL. */
+smap_status smap_reset(smap_handle* h, const double* x0);
+
+/* Sets the particle count of each sequence (host [B], 1..N); NULL = all N.
+ * Only allowed at t = 0 (after create / reset). */
+smap_status smap_set_particle_counts(smap_handle* h, const int* N_per_seq);
+
+/* One online step t -> t+1 of Algorithm 2 for every sequence whose active flag
+ * is set (active: host [B] bytes, or NULL = all): SVGD on the new particle set
+ * (L iterations), then phi_{t+1}, psi_{t+1}. y: [B][dy] FP32 observations z_{t+1}
+ * (host or device per on_device). One fused kernel launch; asynchronous. */
+smap_status smap_step(smap_handle* h, const float* y, const uint8_t* active, int on_device);
+
+/* Backtracking (Section IV-B) for every sequence at its current length T_s:
+ * path [B][max_T+1][d] FP32 (row 0 = x_0^true, rows t > T_s = NaN), J [B]
+ * FP64 = phi_{T_s}(i_{T_s}) (either may be NULL). Synchronises the stream. */
+smap_status smap_map_sequence(smap_handle* h, float* path, double* J, int on_device);
+
+/* The whole batch from t = 0 in one persistent launch (sequences pulled from
+ * a device work queue, longest first), followed by backtracking; the device
+ * work is replayed from a CUDA graph after the first call.
+ * y_all [B][max_T][dy] FP32; T_per_seq host [B] (1..max_T, NULL = max_T);
+ * N_per_seq host [B] (1..N, NULL = N); path / J as in smap_map_sequence.
+ * Afterwards the handle holds the final state (smap_get_history etc.). */
+smap_status smap_run_batch(smap_handle* h, const float* y_all, const int* T_per_seq,
+                           const int* N_per_seq, float* path, double* J, int on_device);
+
+/* Copies of the handle's state: particle sets hist [B][max_T][N][d] FP32 (the
+ * final particles of each step), backpointers psi [B][max_T][N] (psi_1 = 0),
+ * current scores phi [B][N] FP64, current step counts t [B]. */
+smap_status smap_get_history(smap_handle* h, float* hist, int on_device);
+smap_status smap_get_backpointers(smap_handle* h, uint16_t* psi, int on_device);
+smap_status smap_get_scores(smap_handle* h, double* phi, int on_device);
+smap_status smap_get_steps(smap_handle* h, int* t_per_seq);
+
+/* The dynamic programme alone (Eq. forward_recursion + backtracking) over
+ * given particle sets hist [B][max_T][N][d] FP32 and observations y_all
+ * [B][max_T][dy]: the second stage of Algorithm 2 on fixed supports.
+ * T_per_seq / N_per_seq as in smap_run_batch; outputs path / J (may be NULL)
+ * and psi [B][max_T][N] (may be NULL). Uses and overwrites the handle's
+ * history, score and backpointer buffers. Synchronises the stream. */
+smap_status smap_viterbi(smap_handle* h, const float* hist, const float* y_all,
+                         const int* T_per_seq, const int* N_per_seq, float* path,
+                         double* J, uint16_t* psi, int on_device);
+
+/* Kernel variant (particles per thread, block size) used by the step kernels.
+ * smap_autotune times every compiled variant on the first min(B, sample)
+ * sequences for `steps` steps of y_all (layout as in smap_run_batch, host or
+ * device per on_device) and keeps the fastest; the handle is reset afterwards.
+ * variant < 0 in smap_set_variant restores the built-in heuristic. */
+smap_status smap_autotune(smap_handle* h, const float* y_all, int sample, int steps,
+                          int on_device, int* chosen_variant, float* ms_per_variant,
+                          int n_ms);
+smap_status smap_set_variant(smap_handle* h, int variant);
+int smap_num_variants(void);
+smap_status smap_variant_info(int variant, int* particles_per_thread, int* max_threads);
+smap_status smap_get_variant(const smap_handle* h, int* variant, int* threads, int* grid);
+
+/* Debug / parity entry points (host pointers, synchronous).
+ * smap_debug_svgd: n_iters SVGD iterations at step t of every sequence, from
+ * the given initial particles x_init [B][N][d] with the prior built from the
+ * previous set x_prev [B][n_prev][d] (n_prev = 1 and t = 1: x_prev holds
+ * x_0^true, whose transition is taken in FP64 from the handle's x0 instead),
+ * observation y [B][dy]. Writes x_out [B][N][d] and the bandwidth of each
+ * iteration h_out [B][n_iters] (may be NULL). Does not change the handle's
+ * state. */
+smap_status smap_debug_svgd(smap_handle* h, int t, const float* x_prev, int n_prev,
+                            const float* x_init, const float* y, int n_iters,
+                            float* x_out, float* h_out);
+
+/* Raw Philox-4x32-10 words for counters (c0 + k, c1, c2, c3), k < n, key
+ * (key0, key1): out [n][4]; and the standard normals the step kernels draw
+ * for (seed, seq, t, particles i0..i0+n-1, dimension d): normals [n][d]. */
+smap_status smap_debug_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                              uint32_t key0, uint32_t key1, int n, uint32_t* out);
+smap_status smap_debug_normals(uint64_t seed, uint32_t seq, uint32_t t, uint32_t i0,
+                               int n, int d, float* normals);
+
+/* Device times of the last smap_run_batch, in milliseconds, from CUDA events
+ * recorded on the handle's stream inside its graph: seq_kernel_ms around the
+ * persistent step kernel alone, batch_ms around the whole device work (state
+ * reset, step kernel, backtracking). Either pointer may be NULL. */
+smap_status smap_last_kernel_ms(smap_handle* h, float* seq_kernel_ms, float* batch_ms);
+
+/* Kernel launches the library has issued since load (its own kernels only). */
+uint64_t smap_kernel_launches(void);
+
+const char* smap_status_string(smap_status s);
+const char* smap_last_error(const smap_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMAP_H */

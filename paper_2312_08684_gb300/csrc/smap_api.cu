@@ -1,0 +1,896 @@
+// smap_api.cu -- the C ABI of libsmap (declared in include/smap.h): handle,
+// device buffers, launches, the CUDA graph of the batched run, backtracking,
+// the variant autotuner and the debug entry points.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "smap.h"
+#include "smap_internal.h"
+#include "smap_kernels.cuh"
+
+using namespace smap;
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+
+// ---------------------------------------------------------------------------
+// Backtracking (Section IV-B): one warp per sequence. i_T = argmax phi_T
+// (lowest index on ties), i_t = psi_{t+1}(i_{t+1}); path rows gathered from
+// the particle history; J = phi_T(i_T).
+// ---------------------------------------------------------------------------
+__global__ void backtrack_kernel(int B, int Nmax, int maxT, int d, const int* __restrict__ tcur,
+                                 const int* __restrict__ Nseq, const double* __restrict__ phi,
+                                 const uint16_t* __restrict__ psi, const float* __restrict__ hist,
+                                 const double* __restrict__ x0, const int* __restrict__ status,
+                                 int* __restrict__ idxbuf, float* __restrict__ path,
+                                 double* __restrict__ J) {
+    const int warps = blockDim.x >> 5;
+    const int b = blockIdx.x * warps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= B) return;
+    const int T = tcur[b], N = Nseq[b];
+    double bv = -INFINITY;
+    int bi = 0x7fffffff;
+    if (T > 0) {
+        for (int i = lane; i < N; i += 32) {
+            const double v = phi[(size_t)b * Nmax + i];
+            if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    int* idx = idxbuf + (size_t)b * maxT;
+    const bool ok = status[b] == 0 && T <= maxT && N >= 1 && N <= Nmax;
+    if (lane == 0 && T > 0 && ok) {
+        int it = (bi == 0x7fffffff) ? 0 : bi;
+        for (int t = T; t >= 1; --t) {
+            idx[t - 1] = it;
+            if (t > 1) it = min((int)psi[((size_t)b * maxT + (t - 1)) * Nmax + it], N - 1);
+        }
+    }
+    __syncwarp();
+    for (int e = lane; e < (maxT + 1) * d; e += 32) {
+        const int t = e / d, c = e - t * d;
+        float v;
+        if (t == 0) v = (float)x0[(size_t)b * d + c];
+        else if (t <= T && ok) v = hist[(((size_t)b * maxT + (t - 1)) * Nmax + idx[t - 1]) * d + c];
+        else v = __int_as_float(0x7fc00000);
+        path[((size_t)b * (maxT + 1) + t) * d + c] = v;
+    }
+    if (lane == 0) J[b] = (T > 0 && ok) ? bv : (T == 0 ? 0.0 : __longlong_as_double(0x7ff8000000000000LL));
+}
+
+__global__ void philox_kernel(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                              uint32_t k1, int n, uint32_t* out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    uint32_t w[4];
+    philox4x32_10(c0 + (uint32_t)k, c1, c2, c3, k0, k1, w);
+    for (int e = 0; e < 4; ++e) out[(size_t)k * 4 + e] = w[e];
+}
+
+template <int D>
+__global__ void normals_kernel(uint64_t seed, uint32_t seq, uint32_t t, uint32_t i0, int n, float* out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    float z[D];
+    draw_normals<D>(seed, seq, t, i0 + (uint32_t)k, z);
+    for (int c = 0; c < D; ++c) out[(size_t)k * D + c] = z[c];
+}
+
+const ModelKernels* kernels_for(int kind) {
+    static ModelKernels tab[6];
+    static bool init = false;
+    if (!init) {
+        tab[1] = kernels_ngm1d();
+        tab[2] = kernels_range_cv();
+        tab[3] = kernels_clutter_cv();
+        tab[4] = kernels_planar_arm7();
+        tab[5] = kernels_linear_gauss();
+        init = true;
+    }
+    if (kind < 1 || kind > 5) return nullptr;
+    return &tab[kind];
+}
+
+// Fills the device-side model constants; returns false on a bad vector.
+bool make_model(int kind, const double* p, int np, ModelParams& mp, std::string& err) {
+    memset(&mp, 0, sizeof(mp));
+    if (!p || np < 1 || np > kMaxParams) { err = "params: null or bad length"; return false; }
+    mp.kind = kind;
+    mp.np = np;
+    for (int k = 0; k < np; ++k) { mp.p[k] = p[k]; mp.pf[k] = (float)p[k]; }
+    const double two_pi = 6.283185307179586;
+    switch (kind) {
+    case SMAP_MODEL_NGM1D:
+        if (np != 8) { err = "NGM1D expects 8 parameters"; return false; }
+        mp.d = 1; mp.dy = 1; mp.q[0] = p[5];
+        if (!(p[6] > 0)) { err = "NGM1D: r must be > 0"; return false; }
+        mp.aux[0] = -0.5 * std::log(two_pi * p[6]); mp.auxf[0] = (float)(1.0 / p[6]);
+        break;
+    case SMAP_MODEL_RANGE_CV2D: {
+        const int nb = np >= 7 ? (int)p[6] : 0;
+        if (nb < 1 || nb > 8 || np != 7 + 2 * nb) { err = "RANGE_CV2D: expects 7 + 2 nb parameters, nb 1..8"; return false; }
+        if (!(p[5] > 0)) { err = "RANGE_CV2D: r must be > 0"; return false; }
+        mp.d = 4; mp.dy = nb;
+        for (int c = 0; c < 4; ++c) mp.q[c] = p[1 + c];
+        mp.aux[0] = -0.5 * std::log(two_pi * p[5]); mp.auxf[0] = (float)(1.0 / p[5]);
+        break;
+    }
+    case SMAP_MODEL_CLUTTER_CV2D: {
+        if (np != 9) { err = "CLUTTER_CV2D expects 9 parameters"; return false; }
+        const int M = (int)p[6];
+        if (M < 1 || M > 32) { err = "CLUTTER_CV2D: M must be 1..32"; return false; }
+        if (!(p[5] > 0) || !(p[7] > 0 && p[7] < 1) || !(p[8] > 0)) { err = "CLUTTER_CV2D: need r > 0, 0 < beta < 1, area > 0"; return false; }
+        mp.d = 4; mp.dy = 2 * M;
+        for (int c = 0; c < 4; ++c) mp.q[c] = p[1 + c];
+        mp.aux[0] = std::log((1.0 - p[7]) / M) - std::log(two_pi * p[5]);
+        mp.aux[1] = std::log(p[7] / p[8]);
+        mp.auxf[0] = (float)(1.0 / p[5]);
+        mp.auxf[1] = (float)(mp.aux[0] * 1.4426950408889634);
+        mp.auxf[2] = (float)(mp.aux[1] * 1.4426950408889634);
+        break;
+    }
+    case SMAP_MODEL_PLANAR_ARM: {
+        const int nl = np >= 3 ? (int)p[1] : 0;
+        if (nl != 7 || np != 3 + 3 * nl) { err = "PLANAR_ARM: this build compiles nl = 7 (24 parameters)"; return false; }
+        if (!(p[2] > 0)) { err = "PLANAR_ARM: r must be > 0"; return false; }
+        mp.d = 2 * nl; mp.dy = 2;
+        for (int c = 0; c < 2 * nl; ++c) mp.q[c] = p[3 + c];
+        mp.aux[0] = -std::log(two_pi * p[2]); mp.auxf[0] = (float)(1.0 / p[2]);
+        break;
+    }
+    case SMAP_MODEL_LINEAR_GAUSS:
+        if (np != 6) { err = "LINEAR_GAUSS expects 6 parameters"; return false; }
+        if (!(p[5] > 0)) { err = "LINEAR_GAUSS: r must be > 0"; return false; }
+        mp.d = 4; mp.dy = 2;
+        for (int c = 0; c < 4; ++c) mp.q[c] = p[1 + c];
+        mp.aux[0] = -std::log(two_pi * p[5]); mp.auxf[0] = (float)(1.0 / p[5]);
+        break;
+    default:
+        err = "unknown model";
+        return false;
+    }
+    mp.logtrans_c = 0.0;
+    for (int c = 0; c < mp.d; ++c) {
+        if (!(mp.q[c] > 0) || !std::isfinite(mp.q[c])) { err = "process noise variances must be finite and > 0"; return false; }
+        mp.qinv[c] = 1.0 / mp.q[c];
+        mp.sqrt_q[c] = std::sqrt(mp.q[c]);
+        mp.sqrt_qinv[c] = std::sqrt(mp.qinv[c]);
+        mp.qinv_f[c] = (float)mp.qinv[c];
+        mp.sqrt_qinv_f[c] = (float)mp.sqrt_qinv[c];
+        mp.logtrans_c += -0.5 * std::log(two_pi * mp.q[c]);
+    }
+    return true;
+}
+
+}  // namespace
+
+struct smap_handle {
+    smap_config cfg{};
+    std::vector<double> params, x0h;
+    ModelParams mp{};
+    const ModelKernels* K = nullptr;
+    int d = 0, dy = 0, B = 0, Nmax = 0, maxT = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0, num_sms = 0;
+    size_t max_smem = 0;
+    std::string err;
+    bool failed = false;
+    int variant = -1;          // -1: heuristic
+    // device buffers
+    float* hist = nullptr;
+    uint16_t* psi = nullptr;
+    double* phi = nullptr;
+    int* tcur = nullptr;
+    int* Nseq = nullptr;
+    int* Tend = nullptr;
+    int* order = nullptr;
+    double* x0 = nullptr;
+    double* f64 = nullptr;
+    float* bwguess = nullptr;
+    int* status = nullptr;     // [B + 2]: per-sequence status, then median stats
+    int* queue = nullptr;
+    float* y = nullptr;        // [B][maxT][dy]
+    float* ystep = nullptr;    // [B][dy]
+    uint8_t* active = nullptr; // [B]
+    int* idxbuf = nullptr;     // [B][maxT]
+    float* path = nullptr;     // [B][maxT+1][d]
+    double* J = nullptr;       // [B]
+    // host mirrors
+    std::vector<int> tcur_h, Nseq_h, Tend_h;
+    // CUDA graph of the batched run
+    cudaGraphExec_t graph = nullptr;
+    int graph_variant = -2, graph_grid = 0, graph_threads = 0, graph_items = -1;
+    int last_threads = 0, last_grid = 0;
+    bool configured[kNumVariants * 2] = {};
+    // pinned staging of smap_step's inputs; step_done marks when they were consumed
+    float* ystep_h = nullptr;
+    uint8_t* active_h = nullptr;
+    cudaEvent_t step_done = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // batch start, kernel end, batch end
+};
+
+namespace {
+
+smap_status fail(smap_handle* h, smap_status s, const std::string& msg) {
+    if (h) {
+        h->err = msg;
+        if (s == SMAP_E_CUDA) h->failed = true;
+    }
+    return s;
+}
+
+smap_status cuda_fail(smap_handle* h, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(h, SMAP_E_CUDA, m);
+}
+
+#define SMAP_CUDA(h, call)                                      \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+    } while (0)
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Block size of variant v for Nmax particles, or 0 if the variant cannot hold them.
+int variant_threads(int v, int Nmax) {
+    const VariantInfo& vi = kVariants[v];
+    int nt = round_up((Nmax + vi.ppt - 1) / vi.ppt, 32);
+    nt = std::max(nt, 32);
+    return nt <= vi.maxt ? nt : 0;
+}
+
+int heuristic_variant(const smap_handle* h) {
+    if (h->d >= 8) return variant_threads(1, h->Nmax) ? 1 : 2;
+    if (h->Nmax >= 128 && variant_threads(3, h->Nmax)) return 3;
+    if (variant_threads(0, h->Nmax)) return 0;
+    return variant_threads(1, h->Nmax) ? 1 : 2;
+}
+
+smap_status configure_kernel(smap_handle* h, const void* fn, size_t smem) {
+    if (smem > h->max_smem)
+        return fail(h, SMAP_E_UNSUPPORTED, "shared memory need exceeds the device limit for this N and d");
+    for (int k = 0; k < kNumVariants; ++k) {
+        bool* flag = fn == h->K->seq[k] ? &h->configured[k] : fn == h->K->dbg[k] ? &h->configured[kNumVariants + k] : nullptr;
+        if (!flag) continue;
+        if (!*flag) {
+            SMAP_CUDA(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            *flag = true;
+        }
+        return SMAP_OK;
+    }
+    SMAP_CUDA(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return SMAP_OK;
+}
+
+// Launches the sequence kernel of variant v over `items` work items.
+smap_status launch_seq(smap_handle* h, int v, int items, int mode, const float* y, int viterbi_only,
+                       const int* order, int* grid_out = nullptr, int* threads_out = nullptr) {
+    const int nt = variant_threads(v, h->Nmax);
+    if (!nt) return fail(h, SMAP_E_UNSUPPORTED, "kernel variant cannot hold N particles");
+    const void* fn = h->K->seq[v];
+    const size_t smem = smem_layout(h->Nmax, h->K->DP).total;
+    smap_status st = configure_kernel(h, fn, smem);
+    if (st) return st;
+    int occ = 0;
+    SMAP_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nt, smem));
+    if (occ < 1) return fail(h, SMAP_E_UNSUPPORTED, "kernel variant does not fit on an SM");
+    const int grid = std::max(1, std::min(items, occ * h->num_sms));
+    SeqArgs a;
+    memset(&a, 0, sizeof(a));
+    a.mp = h->mp;
+    a.B = items;
+    a.Nmax = h->Nmax;
+    a.maxT = h->maxT;
+    a.L = h->cfg.L;
+    a.bw_rule = h->cfg.bw_rule;
+    a.prior = h->cfg.prior;
+    a.mode = mode;
+    a.eps = (float)h->cfg.step;
+    a.bw_value = (float)h->cfg.bw_value;
+    a.seed = h->cfg.seed;
+    a.y = y;
+    a.x0 = h->x0;
+    a.hist = h->hist;
+    a.psi = h->psi;
+    a.phi = h->phi;
+    a.tcur = h->tcur;
+    a.Nseq = h->Nseq;
+    a.Tend = h->Tend;
+    a.active = (mode == 1) ? h->active : nullptr;
+    a.order = order;
+    a.f64 = h->f64;
+    a.bwguess = h->bwguess;
+    a.status = h->status;
+    a.queue = h->queue;
+    a.viterbi_only = viterbi_only;
+    void* args[] = {&a};
+    SMAP_CUDA(h, cudaMemsetAsync(h->queue, 0, sizeof(int), h->stream));
+    SMAP_CUDA(h, cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, smem, h->stream));
+    SMAP_CUDA(h, cudaGetLastError());
+    g_launches.fetch_add(1);
+    h->last_threads = nt;
+    h->last_grid = grid;
+    if (grid_out) *grid_out = grid;
+    if (threads_out) *threads_out = nt;
+    return SMAP_OK;
+}
+
+smap_status launch_backtrack(smap_handle* h) {
+    const int warps = 4;
+    const int grid = (h->B + warps - 1) / warps;
+    backtrack_kernel<<<grid, 32 * warps, 0, h->stream>>>(h->B, h->Nmax, h->maxT, h->d, h->tcur, h->Nseq,
+                                                         h->phi, h->psi, h->hist, h->x0, h->status,
+                                                         h->idxbuf, h->path, h->J);
+    SMAP_CUDA(h, cudaGetLastError());
+    g_launches.fetch_add(1);
+    return SMAP_OK;
+}
+
+smap_status check_usable(smap_handle* h) {
+    if (!h) return SMAP_E_INVAL;
+    if (h->failed) return SMAP_E_STATE;
+    return SMAP_OK;
+}
+
+cudaMemcpyKind kind_in(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+cudaMemcpyKind kind_out(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+// Reads the per-sequence status words; returns the first failure or OK.
+smap_status collect_status(smap_handle* h) {
+    std::vector<int> st(h->B);
+    SMAP_CUDA(h, cudaMemcpyAsync(st.data(), h->status, sizeof(int) * h->B, cudaMemcpyDeviceToHost, h->stream));
+    SMAP_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (int b = 0; b < h->B; ++b) {
+        if (st[b] == SMAP_E_NONFINITE)
+            return fail(h, SMAP_E_NONFINITE, "sequence " + std::to_string(b) + ": particles or scores became non-finite");
+        if (st[b] != 0)
+            return fail(h, SMAP_E_INVAL, "sequence " + std::to_string(b) + ": rejected by the kernel (length or particle count)");
+    }
+    return SMAP_OK;
+}
+
+smap_status upload_counts(smap_handle* h, const int* T_per_seq, const int* N_per_seq) {
+    for (int b = 0; b < h->B; ++b) {
+        const int T = T_per_seq ? T_per_seq[b] : h->maxT;
+        const int N = N_per_seq ? N_per_seq[b] : h->Nmax;
+        if (T < 1 || T > h->maxT) return fail(h, SMAP_E_INVAL, "T_per_seq out of 1..max_T");
+        if (N < 1 || N > h->Nmax) return fail(h, SMAP_E_INVAL, "N_per_seq out of 1..N");
+        h->Tend_h[b] = T;
+        h->Nseq_h[b] = N;
+    }
+    // longest work first: T N^2 decreasing
+    std::vector<int> ord(h->B);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+        return (double)h->Tend_h[a] * h->Nseq_h[a] * h->Nseq_h[a] > (double)h->Tend_h[b] * h->Nseq_h[b] * h->Nseq_h[b];
+    });
+    SMAP_CUDA(h, cudaMemcpyAsync(h->Tend, h->Tend_h.data(), sizeof(int) * h->B, cudaMemcpyHostToDevice, h->stream));
+    SMAP_CUDA(h, cudaMemcpyAsync(h->Nseq, h->Nseq_h.data(), sizeof(int) * h->B, cudaMemcpyHostToDevice, h->stream));
+    SMAP_CUDA(h, cudaMemcpyAsync(h->order, ord.data(), sizeof(int) * h->B, cudaMemcpyHostToDevice, h->stream));
+    SMAP_CUDA(h, cudaStreamSynchronize(h->stream));   // host vectors above are temporaries
+    return SMAP_OK;
+}
+
+smap_status reset_device_state(smap_handle* h) {
+    SMAP_CUDA(h, cudaMemsetAsync(h->tcur, 0, sizeof(int) * h->B, h->stream));
+    SMAP_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(int) * (h->B + 2), h->stream));
+    SMAP_CUDA(h, cudaMemsetAsync(h->bwguess, 0, sizeof(float) * h->B, h->stream));
+    return SMAP_OK;
+}
+
+smap_status copy_outputs(smap_handle* h, float* path, double* J, int on_device) {
+    if (path)
+        SMAP_CUDA(h, cudaMemcpyAsync(path, h->path, sizeof(float) * (size_t)h->B * (h->maxT + 1) * h->d,
+                                     kind_out(on_device), h->stream));
+    if (J) SMAP_CUDA(h, cudaMemcpyAsync(J, h->J, sizeof(double) * h->B, kind_out(on_device), h->stream));
+    SMAP_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SMAP_OK;
+}
+
+// The device work of one batched run: state reset, the persistent kernel
+// over all sequences, backtracking. Recorded once into a CUDA graph.
+smap_status batch_device_work(smap_handle* h, int v) {
+    SMAP_CUDA(h, cudaEventRecord(h->ev[0], h->stream));
+    smap_status st = reset_device_state(h);
+    if (st) return st;
+    st = launch_seq(h, v, h->B, 0, h->y, 0, h->order);
+    if (st) return st;
+    SMAP_CUDA(h, cudaEventRecord(h->ev[1], h->stream));
+    st = launch_backtrack(h);
+    if (st) return st;
+    SMAP_CUDA(h, cudaEventRecord(h->ev[2], h->stream));
+    return SMAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* smap_status_string(smap_status s) {
+    switch (s) {
+    case SMAP_OK: return "ok";
+    case SMAP_E_INVAL: return "invalid argument";
+    case SMAP_E_NOMEM: return "out of memory";
+    case SMAP_E_CUDA: return "CUDA error";
+    case SMAP_E_STATE: return "handle in a failed state or call out of order";
+    case SMAP_E_TIMEOUT: return "bounded wait ran out";
+    case SMAP_E_NONFINITE: return "non-finite particles or observations";
+    case SMAP_E_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* smap_last_error(const smap_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+uint64_t smap_kernel_launches(void) { return g_launches.load(); }
+
+smap_status smap_last_kernel_ms(smap_handle* h, float* seq_ms, float* batch_ms) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    if (!h->graph) return fail(h, SMAP_E_STATE, "no batched run yet");
+    SMAP_CUDA(h, cudaEventSynchronize(h->ev[2]));
+    if (seq_ms) SMAP_CUDA(h, cudaEventElapsedTime(seq_ms, h->ev[0], h->ev[1]));
+    if (batch_ms) SMAP_CUDA(h, cudaEventElapsedTime(batch_ms, h->ev[0], h->ev[2]));
+    return SMAP_OK;
+}
+
+int smap_num_variants(void) { return kNumVariants; }
+
+smap_status smap_variant_info(int v, int* ppt, int* maxt) {
+    if (v < 0 || v >= kNumVariants) return SMAP_E_INVAL;
+    if (ppt) *ppt = kVariants[v].ppt;
+    if (maxt) *maxt = kVariants[v].maxt;
+    return SMAP_OK;
+}
+
+void smap_destroy(smap_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->step_done) cudaEventDestroy(h->step_done);
+    for (cudaEvent_t ev : h->ev)
+        if (ev) cudaEventDestroy(ev);
+    if (h->ystep_h) cudaFreeHost(h->ystep_h);
+    if (h->active_h) cudaFreeHost(h->active_h);
+    void* bufs[] = {h->hist, h->psi, h->phi, h->tcur, h->Nseq, h->Tend, h->order, h->x0, h->f64,
+                    h->bwguess, h->status, h->queue, h->y, h->ystep, h->active, h->idxbuf, h->path, h->J};
+    for (void* p : bufs)
+        if (p) cudaFree(p);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+smap_status smap_create(const smap_config* cfg, smap_handle** out) {
+    if (!out) return SMAP_E_INVAL;
+    *out = nullptr;
+    if (!cfg) return SMAP_E_INVAL;
+    smap_handle* h = new smap_handle();
+    h->cfg = *cfg;
+    auto bail = [&](smap_status s, const std::string& msg) {
+        std::fprintf(stderr, "smap_create: %s\n", msg.c_str());
+        smap_destroy(h);
+        return s;
+    };
+    h->K = kernels_for(cfg->model);
+    if (!h->K) return bail(SMAP_E_INVAL, "unknown model");
+    std::string err;
+    if (!make_model(cfg->model, cfg->params, cfg->n_params, h->mp, err)) return bail(SMAP_E_INVAL, err);
+    h->params.assign(cfg->params, cfg->params + cfg->n_params);
+    h->cfg.params = h->params.data();
+    h->d = h->mp.d;
+    h->dy = h->mp.dy;
+    if (h->d != h->K->D) return bail(SMAP_E_INVAL, "state dimension does not match the compiled model");
+    if (cfg->N < 1 || cfg->N > kMaxN) return bail(SMAP_E_INVAL, "N out of 1..4096");
+    if (cfg->L < 0) return bail(SMAP_E_INVAL, "L < 0");
+    if (cfg->batch < 1) return bail(SMAP_E_INVAL, "batch < 1");
+    if (cfg->max_T < 1) return bail(SMAP_E_INVAL, "max_T < 1");
+    if (!(std::isfinite(cfg->step))) return bail(SMAP_E_INVAL, "step not finite");
+    if (cfg->bw_rule < 0 || cfg->bw_rule > 2) return bail(SMAP_E_INVAL, "bw_rule");
+    if (!(cfg->bw_value > 0) || !std::isfinite(cfg->bw_value)) return bail(SMAP_E_INVAL, "bw_value must be > 0");
+    if (cfg->prior < 0 || cfg->prior > 1) return bail(SMAP_E_INVAL, "prior");
+    if (!cfg->x0) return bail(SMAP_E_INVAL, "x0 is null");
+    h->B = cfg->batch;
+    h->Nmax = cfg->N;
+    h->maxT = cfg->max_T;
+    h->x0h.assign(cfg->x0, cfg->x0 + (size_t)h->B * h->d);
+    for (double v : h->x0h)
+        if (!std::isfinite(v)) return bail(SMAP_E_NONFINITE, "x0 not finite");
+    h->cfg.x0 = h->x0h.data();
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return bail(SMAP_E_CUDA, cudaGetErrorString(e));
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, h->device);
+    if (e != cudaSuccess) return bail(SMAP_E_CUDA, cudaGetErrorString(e));
+    h->num_sms = prop.multiProcessorCount;
+    h->max_smem = prop.sharedMemPerBlockOptin;
+    if (smem_layout(h->Nmax, h->K->DP).total > h->max_smem)
+        return bail(SMAP_E_UNSUPPORTED, "N too large for shared memory at this state dimension");
+    if (cfg->stream) {
+        h->stream = (cudaStream_t)cfg->stream;
+    } else {
+        e = cudaStreamCreate(&h->stream);
+        if (e != cudaSuccess) return bail(SMAP_E_CUDA, cudaGetErrorString(e));
+        h->own_stream = true;
+    }
+    const size_t B = h->B, N = h->Nmax, T = h->maxT, d = h->d, dy = h->dy;
+    struct A { void** p; size_t bytes; } allocs[] = {
+        {(void**)&h->hist, sizeof(float) * B * T * N * d},
+        {(void**)&h->psi, sizeof(uint16_t) * B * T * N},
+        {(void**)&h->phi, sizeof(double) * B * N},
+        {(void**)&h->tcur, sizeof(int) * B},
+        {(void**)&h->Nseq, sizeof(int) * B},
+        {(void**)&h->Tend, sizeof(int) * B},
+        {(void**)&h->order, sizeof(int) * B},
+        {(void**)&h->x0, sizeof(double) * B * d},
+        {(void**)&h->f64, sizeof(double) * B * N * d},
+        {(void**)&h->bwguess, sizeof(float) * B},
+        {(void**)&h->status, sizeof(int) * (B + 2)},
+        {(void**)&h->queue, sizeof(int) * 4},
+        {(void**)&h->y, sizeof(float) * B * T * dy},
+        {(void**)&h->ystep, sizeof(float) * B * dy},
+        {(void**)&h->active, B},
+        {(void**)&h->idxbuf, sizeof(int) * B * T},
+        {(void**)&h->path, sizeof(float) * B * (T + 1) * d},
+        {(void**)&h->J, sizeof(double) * B},
+    };
+    for (auto& al : allocs) {
+        e = cudaMalloc(al.p, al.bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bail(SMAP_E_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+    }
+    if (cudaMallocHost(&h->ystep_h, sizeof(float) * B * dy) != cudaSuccess ||
+        cudaMallocHost(&h->active_h, B) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(SMAP_E_NOMEM, "cudaMallocHost failed");
+    }
+    e = cudaEventCreateWithFlags(&h->step_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bail(SMAP_E_CUDA, cudaGetErrorString(e));
+    for (cudaEvent_t& ev : h->ev) {
+        e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return bail(SMAP_E_CUDA, cudaGetErrorString(e));
+    }
+    h->tcur_h.assign(B, 0);
+    h->Nseq_h.assign(B, (int)N);
+    h->Tend_h.assign(B, (int)T);
+    e = cudaMemcpy(h->x0, h->x0h.data(), sizeof(double) * B * d, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(SMAP_E_CUDA, cudaGetErrorString(e));
+    if (upload_counts(h, nullptr, nullptr) != SMAP_OK) return bail(SMAP_E_CUDA, h->err);
+    if (reset_device_state(h) != SMAP_OK) return bail(SMAP_E_CUDA, h->err);
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return bail(SMAP_E_CUDA, cudaGetErrorString(e));
+    h->variant = -1;
+    *out = h;
+    return SMAP_OK;
+}
+
+smap_status smap_dims(const smap_handle* h, int* d, int* dy) {
+    if (!h) return SMAP_E_INVAL;
+    if (d) *d = h->d;
+    if (dy) *dy = h->dy;
+    return SMAP_OK;
+}
+
+smap_status smap_reset(smap_handle* h, const double* x0) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    if (x0) {
+        for (size_t k = 0; k < (size_t)h->B * h->d; ++k)
+            if (!std::isfinite(x0[k])) return fail(h, SMAP_E_NONFINITE, "x0 not finite");
+        h->x0h.assign(x0, x0 + (size_t)h->B * h->d);
+        SMAP_CUDA(h, cudaMemcpyAsync(h->x0, h->x0h.data(), sizeof(double) * h->x0h.size(),
+                                     cudaMemcpyHostToDevice, h->stream));
+    }
+    std::fill(h->tcur_h.begin(), h->tcur_h.end(), 0);
+    st = reset_device_state(h);
+    if (st) return st;
+    SMAP_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SMAP_OK;
+}
+
+smap_status smap_set_particle_counts(smap_handle* h, const int* N_per_seq) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    for (int b = 0; b < h->B; ++b)
+        if (h->tcur_h[b] != 0) return fail(h, SMAP_E_STATE, "particle counts can only change at t = 0");
+    return upload_counts(h, h->Tend_h.data(), N_per_seq);
+}
+
+smap_status smap_set_variant(smap_handle* h, int v) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    if (v >= kNumVariants) return fail(h, SMAP_E_INVAL, "variant out of range");
+    if (v >= 0 && !variant_threads(v, h->Nmax)) return fail(h, SMAP_E_UNSUPPORTED, "variant cannot hold N particles");
+    h->variant = v < 0 ? -1 : v;
+    return SMAP_OK;
+}
+
+smap_status smap_get_variant(const smap_handle* h, int* v, int* threads, int* grid) {
+    if (!h) return SMAP_E_INVAL;
+    const int vv = h->variant >= 0 ? h->variant : heuristic_variant(h);
+    if (v) *v = vv;
+    if (threads) *threads = variant_threads(vv, h->Nmax);
+    if (grid) *grid = h->last_grid;
+    return SMAP_OK;
+}
+
+smap_status smap_step(smap_handle* h, const float* y, const uint8_t* active, int on_device) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    if (!y) return fail(h, SMAP_E_INVAL, "y is null");
+    for (int b = 0; b < h->B; ++b)
+        if ((!active || active[b]) && h->tcur_h[b] >= h->maxT)
+            return fail(h, SMAP_E_INVAL, "a sequence is already at max_T");
+    if (!on_device) {
+        for (size_t k = 0; k < (size_t)h->B * h->dy; ++k)
+            if (std::isinf(y[k])) return fail(h, SMAP_E_NONFINITE, "observation is infinite");
+    }
+    // the pinned staging buffers may still feed the previous step's copies
+    SMAP_CUDA(h, cudaEventSynchronize(h->step_done));
+    if (on_device) {
+        SMAP_CUDA(h, cudaMemcpyAsync(h->ystep, y, sizeof(float) * h->B * h->dy, cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+        memcpy(h->ystep_h, y, sizeof(float) * h->B * h->dy);
+        SMAP_CUDA(h, cudaMemcpyAsync(h->ystep, h->ystep_h, sizeof(float) * h->B * h->dy, cudaMemcpyHostToDevice, h->stream));
+    }
+    for (int b = 0; b < h->B; ++b) h->active_h[b] = (!active || active[b]) ? 1 : 0;
+    SMAP_CUDA(h, cudaMemcpyAsync(h->active, h->active_h, h->B, cudaMemcpyHostToDevice, h->stream));
+    SMAP_CUDA(h, cudaEventRecord(h->step_done, h->stream));
+    const int v = h->variant >= 0 ? h->variant : heuristic_variant(h);
+    st = launch_seq(h, v, h->B, 1, h->ystep, 0, nullptr);
+    if (st) return st;
+    for (int b = 0; b < h->B; ++b)
+        if (h->active_h[b]) h->tcur_h[b] += 1;
+    return SMAP_OK;
+}
+
+smap_status smap_map_sequence(smap_handle* h, float* path, double* J, int on_device) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    st = launch_backtrack(h);
+    if (st) return st;
+    st = copy_outputs(h, path, J, on_device);
+    if (st) return st;
+    return collect_status(h);
+}
+
+smap_status smap_run_batch(smap_handle* h, const float* y_all, const int* T_per_seq, const int* N_per_seq,
+                           float* path, double* J, int on_device) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    if (!y_all) return fail(h, SMAP_E_INVAL, "y_all is null");
+    st = upload_counts(h, T_per_seq, N_per_seq);
+    if (st) return st;
+    SMAP_CUDA(h, cudaMemcpyAsync(h->y, y_all, sizeof(float) * (size_t)h->B * h->maxT * h->dy,
+                                 kind_in(on_device), h->stream));
+    const int v = h->variant >= 0 ? h->variant : heuristic_variant(h);
+    if (!variant_threads(v, h->Nmax)) return fail(h, SMAP_E_UNSUPPORTED, "kernel variant cannot hold N particles");
+    st = configure_kernel(h, h->K->seq[v], smem_layout(h->Nmax, h->K->DP).total);
+    if (st) return st;
+    if (!h->graph || h->graph_variant != v) {
+        if (h->graph) {
+            cudaGraphExecDestroy(h->graph);
+            h->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        SMAP_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        const uint64_t before = g_launches.load();
+        smap_status cst = batch_device_work(h, v);
+        cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
+        g_launches.store(before);   // capture records launches; they run at replay
+        if (cst) {
+            if (g) cudaGraphDestroy(g);
+            return cst;
+        }
+        if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaStreamEndCapture");
+        ce = cudaGraphInstantiate(&h->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaGraphInstantiate");
+        h->graph_variant = v;
+    }
+    SMAP_CUDA(h, cudaGraphLaunch(h->graph, h->stream));
+    g_launches.fetch_add(2);
+    for (int b = 0; b < h->B; ++b) h->tcur_h[b] = h->Tend_h[b];
+    st = copy_outputs(h, path, J, on_device);
+    if (st) return st;
+    return collect_status(h);
+}
+
+smap_status smap_get_history(smap_handle* h, float* hist, int on_device) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    if (!hist) return fail(h, SMAP_E_INVAL, "null output");
+    SMAP_CUDA(h, cudaMemcpyAsync(hist, h->hist, sizeof(float) * (size_t)h->B * h->maxT * h->Nmax * h->d,
+                                 kind_out(on_device), h->stream));
+    SMAP_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SMAP_OK;
+}
+
+smap_status smap_get_backpointers(smap_handle* h, uint16_t* psi, int on_device) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    if (!psi) return fail(h, SMAP_E_INVAL, "null output");
+    SMAP_CUDA(h, cudaMemcpyAsync(psi, h->psi, sizeof(uint16_t) * (size_t)h->B * h->maxT * h->Nmax,
+                                 kind_out(on_device), h->stream));
+    SMAP_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SMAP_OK;
+}
+
+smap_status smap_get_scores(smap_handle* h, double* phi, int on_device) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    if (!phi) return fail(h, SMAP_E_INVAL, "null output");
+    SMAP_CUDA(h, cudaMemcpyAsync(phi, h->phi, sizeof(double) * (size_t)h->B * h->Nmax, kind_out(on_device), h->stream));
+    SMAP_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SMAP_OK;
+}
+
+smap_status smap_get_steps(smap_handle* h, int* t) {
+    if (!h || !t) return SMAP_E_INVAL;
+    std::copy(h->tcur_h.begin(), h->tcur_h.end(), t);
+    return SMAP_OK;
+}
+
+smap_status smap_viterbi(smap_handle* h, const float* hist, const float* y_all, const int* T_per_seq,
+                         const int* N_per_seq, float* path, double* J, uint16_t* psi, int on_device) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    if (!hist || !y_all) return fail(h, SMAP_E_INVAL, "null input");
+    st = upload_counts(h, T_per_seq, N_per_seq);
+    if (st) return st;
+    SMAP_CUDA(h, cudaMemcpyAsync(h->hist, hist, sizeof(float) * (size_t)h->B * h->maxT * h->Nmax * h->d,
+                                 kind_in(on_device), h->stream));
+    SMAP_CUDA(h, cudaMemcpyAsync(h->y, y_all, sizeof(float) * (size_t)h->B * h->maxT * h->dy,
+                                 kind_in(on_device), h->stream));
+    st = reset_device_state(h);
+    if (st) return st;
+    const int v = h->variant >= 0 ? h->variant : heuristic_variant(h);
+    st = launch_seq(h, v, h->B, 0, h->y, 1, h->order);
+    if (st) return st;
+    st = launch_backtrack(h);
+    if (st) return st;
+    for (int b = 0; b < h->B; ++b) h->tcur_h[b] = h->Tend_h[b];
+    if (psi)
+        SMAP_CUDA(h, cudaMemcpyAsync(psi, h->psi, sizeof(uint16_t) * (size_t)h->B * h->maxT * h->Nmax,
+                                     kind_out(on_device), h->stream));
+    st = copy_outputs(h, path, J, on_device);
+    if (st) return st;
+    return collect_status(h);
+}
+
+smap_status smap_autotune(smap_handle* h, const float* y_all, int sample, int steps, int on_device,
+                          int* chosen, float* ms_per_variant, int n_ms) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    if (!y_all || sample < 1 || steps < 1) return fail(h, SMAP_E_INVAL, "autotune: bad arguments");
+    const int items = std::min(sample, h->B);
+    const int T = std::min(steps, h->maxT);
+    std::vector<int> Tl(h->B, T);
+    st = upload_counts(h, Tl.data(), h->Nseq_h.data());
+    if (st) return st;
+    SMAP_CUDA(h, cudaMemcpyAsync(h->y, y_all, sizeof(float) * (size_t)h->B * h->maxT * h->dy,
+                                 kind_in(on_device), h->stream));
+    cudaEvent_t e0, e1;
+    SMAP_CUDA(h, cudaEventCreate(&e0));
+    SMAP_CUDA(h, cudaEventCreate(&e1));
+    int best = -1;
+    float best_ms = INFINITY;
+    for (int v = 0; v < kNumVariants; ++v) {
+        float ms = INFINITY;
+        const size_t smem = smem_layout(h->Nmax, h->K->DP).total;
+        int occ = 0;
+        if (variant_threads(v, h->Nmax) && smem <= h->max_smem &&
+            configure_kernel(h, h->K->seq[v], smem) == SMAP_OK &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, h->K->seq[v], variant_threads(v, h->Nmax), smem) == cudaSuccess &&
+            occ > 0) {
+            for (int rep = 0; rep < 2; ++rep) {   // first run warms up
+                if ((st = reset_device_state(h))) break;
+                SMAP_CUDA(h, cudaEventRecord(e0, h->stream));
+                if ((st = launch_seq(h, v, items, 0, h->y, 0, h->order))) break;
+                SMAP_CUDA(h, cudaEventRecord(e1, h->stream));
+                SMAP_CUDA(h, cudaEventSynchronize(e1));
+                SMAP_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
+            }
+            if (st) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+        }
+        cudaGetLastError();
+        if (ms_per_variant && v < n_ms) ms_per_variant[v] = ms;
+        if (ms < best_ms) { best_ms = ms; best = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best < 0) return fail(h, SMAP_E_UNSUPPORTED, "no kernel variant fits");
+    h->variant = best;
+    if (chosen) *chosen = best;
+    std::vector<int> Tfull(h->B, h->maxT);
+    st = upload_counts(h, Tfull.data(), h->Nseq_h.data());
+    if (st) return st;
+    return smap_reset(h, nullptr);
+}
+
+smap_status smap_debug_svgd(smap_handle* h, int t, const float* x_prev, int n_prev, const float* x_init,
+                            const float* y, int n_iters, float* x_out, float* h_out) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    if (!x_prev || !x_init || !y || !x_out || t < 1 || n_iters < 0) return fail(h, SMAP_E_INVAL, "debug_svgd: bad arguments");
+    if (n_prev != 1 && n_prev != h->Nmax) return fail(h, SMAP_E_INVAL, "debug_svgd: n_prev must be 1 or N");
+    const size_t B = h->B, N = h->Nmax, d = h->d;
+    float *dxp = nullptr, *dxi = nullptr, *dy = nullptr, *dxo = nullptr, *dho = nullptr;
+    double* df = nullptr;
+    auto cleanup = [&]() { cudaFree(dxp); cudaFree(dxi); cudaFree(dy); cudaFree(dxo); cudaFree(dho); cudaFree(df); };
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc(&dxp, sizeof(float) * B * n_prev * d)) || (e = cudaMalloc(&dxi, sizeof(float) * B * N * d)) ||
+        (e = cudaMalloc(&dy, sizeof(float) * B * h->dy)) || (e = cudaMalloc(&dxo, sizeof(float) * B * N * d)) ||
+        (e = cudaMalloc(&dho, sizeof(float) * B * std::max(n_iters, 1))) || (e = cudaMalloc(&df, sizeof(double) * B * n_prev * d))) {
+        cleanup();
+        return cuda_fail(h, e, "debug_svgd cudaMalloc");
+    }
+    cudaMemcpy(dxp, x_prev, sizeof(float) * B * n_prev * d, cudaMemcpyHostToDevice);
+    cudaMemcpy(dxi, x_init, sizeof(float) * B * N * d, cudaMemcpyHostToDevice);
+    cudaMemcpy(dy, y, sizeof(float) * B * h->dy, cudaMemcpyHostToDevice);
+    DebugSvgdArgs a;
+    memset(&a, 0, sizeof(a));
+    a.mp = h->mp;
+    a.B = (int)B; a.N = (int)N; a.Np = n_prev; a.t = t; a.iters = n_iters;
+    a.bw_rule = h->cfg.bw_rule; a.prior = h->cfg.prior;
+    a.eps = (float)h->cfg.step; a.bw_value = (float)h->cfg.bw_value;
+    a.xprev = dxp; a.x0 = h->x0; a.xinit = dxi; a.y = dy; a.xout = dxo; a.hout = dho; a.f64 = df;
+    const int v = h->variant >= 0 ? h->variant : heuristic_variant(h);
+    const int nt = variant_threads(v, h->Nmax);
+    const size_t smem = smem_layout(h->Nmax, h->K->DP).total;
+    if ((st = configure_kernel(h, h->K->dbg[v], smem))) { cleanup(); return st; }
+    void* args[] = {&a};
+    e = cudaLaunchKernel(h->K->dbg[v], dim3((unsigned)B), dim3(nt), args, smem, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    g_launches.fetch_add(1);
+    if (e == cudaSuccess) e = cudaMemcpy(x_out, dxo, sizeof(float) * B * N * d, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h_out && n_iters > 0) e = cudaMemcpy(h_out, dho, sizeof(float) * B * n_iters, cudaMemcpyDeviceToHost);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(h, e, "debug_svgd");
+    return SMAP_OK;
+}
+
+smap_status smap_debug_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t key0, uint32_t key1,
+                              int n, uint32_t* out) {
+    if (n < 1 || !out) return SMAP_E_INVAL;
+    uint32_t* d = nullptr;
+    if (cudaMalloc(&d, sizeof(uint32_t) * 4 * n) != cudaSuccess) return SMAP_E_NOMEM;
+    philox_kernel<<<(n + 255) / 256, 256>>>(c0, c1, c2, c3, key0, key1, n, d);
+    g_launches.fetch_add(1);
+    cudaError_t e = cudaMemcpy(out, d, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e == cudaSuccess ? SMAP_OK : SMAP_E_CUDA;
+}
+
+smap_status smap_debug_normals(uint64_t seed, uint32_t seq, uint32_t t, uint32_t i0, int n, int d, float* out) {
+    if (n < 1 || !out) return SMAP_E_INVAL;
+    if (d != 1 && d != 4 && d != 14) return SMAP_E_UNSUPPORTED;
+    float* dv = nullptr;
+    if (cudaMalloc(&dv, sizeof(float) * d * n) != cudaSuccess) return SMAP_E_NOMEM;
+    const int g = (n + 255) / 256;
+    if (d == 1) normals_kernel<1><<<g, 256>>>(seed, seq, t, i0, n, dv);
+    else if (d == 4) normals_kernel<4><<<g, 256>>>(seed, seq, t, i0, n, dv);
+    else normals_kernel<14><<<g, 256>>>(seed, seq, t, i0, n, dv);
+    g_launches.fetch_add(1);
+    cudaError_t e = cudaMemcpy(out, dv, sizeof(float) * d * n, cudaMemcpyDeviceToHost);
+    cudaFree(dv);
+    return e == cudaSuccess ? SMAP_OK : SMAP_E_CUDA;
+}
+
+}  // extern "C"

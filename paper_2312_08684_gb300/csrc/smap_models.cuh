@@ -1,0 +1,215 @@
+// smap_models.cuh -- the scenario models as device functions.
+//
+// Each model provides, with D the state dimension and DP the shared-memory row
+// stride of a particle:
+//   step_const(mp, t)               FP64 constant of the transition at step t
+//   transition(mp, sc, x, f)        f = f_t(x) in FP32          (Eq. SSM-x mean)
+//   transition64(mp, sc, x, f)      the same in FP64
+//   grad_loglik(mp, z, x, g)        grad_x log p(z | x) in FP32 (Eq. SSM-z)
+//   loglik64(mp, z, x)              log p(z | x) in FP64, full normaliser
+// Parameter layouts are documented in include/smap.h; aux[] holds constants
+// the host precomputes in FP64 (listed per model).
+#pragma once
+
+#include "smap_common.cuh"
+
+namespace smap {
+
+// 1-D nonstationary growth model. p = [a, b, c, omega, t_off, q, r, hcoef].
+// aux[0] = -1/2 log(2 pi r), auxf[0] = 1/r.
+struct ModelNGM1D {
+    static constexpr int KIND = 1, D = 1, DP = 1, DY = 1;
+    __device__ static double step_const(const ModelParams& mp, int t) {
+        return mp.p[2] * cos(mp.p[3] * ((double)t + mp.p[4]));
+    }
+    __device__ static void transition(const ModelParams& mp, double sc, const float* x, float* f) {
+        const float v = x[0];
+        f[0] = mp.pf[0] * v + mp.pf[1] * v / (1.0f + v * v) + (float)sc;
+    }
+    __device__ static void transition64(const ModelParams& mp, double sc, const double* x, double* f) {
+        const double v = x[0];
+        f[0] = mp.p[0] * v + mp.p[1] * v / (1.0 + v * v) + sc;
+    }
+    __device__ static void grad_loglik(const ModelParams& mp, const float* z, const float* x, float* g) {
+        const float res = z[0] - mp.pf[7] * x[0] * x[0];
+        g[0] = res * mp.auxf[0] * 2.0f * mp.pf[7] * x[0];
+    }
+    __device__ static double loglik64(const ModelParams& mp, const float* z, const double* x) {
+        const double res = (double)z[0] - mp.p[7] * x[0] * x[0];
+        return -0.5 * res * res / mp.p[6] + mp.aux[0];
+    }
+};
+
+// Constant-velocity transition shared by the three planar-target models.
+struct CVTransition {
+    __device__ static double step_const(const ModelParams&, int) { return 0.0; }
+    __device__ static void transition(const ModelParams& mp, double, const float* x, float* f) {
+        const float dt = mp.pf[0];
+        f[0] = fmaf(dt, x[2], x[0]);
+        f[1] = fmaf(dt, x[3], x[1]);
+        f[2] = x[2];
+        f[3] = x[3];
+    }
+    __device__ static void transition64(const ModelParams& mp, double, const double* x, double* f) {
+        const double dt = mp.p[0];
+        f[0] = x[0] + dt * x[2];
+        f[1] = x[1] + dt * x[3];
+        f[2] = x[2];
+        f[3] = x[3];
+    }
+};
+
+// Range-only localisation. p = [dt, q0..q3, r, nb, b0x, b0y, ...].
+// aux[0] = -1/2 log(2 pi r), auxf[0] = 1/r. NaN observation = beacon not heard.
+struct ModelRangeCV : CVTransition {
+    static constexpr int KIND = 2, D = 4, DP = 4, DY = 8;
+    __device__ static void grad_loglik(const ModelParams& mp, const float* z, const float* x, float* g) {
+        const int nb = (int)mp.p[6];
+        float g0 = 0.0f, g1 = 0.0f;
+        for (int l = 0; l < nb; ++l) {
+            const float zl = z[l];
+            if (zl != zl) continue;
+            const float dx = x[0] - mp.pf[7 + 2 * l], dy = x[1] - mp.pf[8 + 2 * l];
+            float rho = sqrtf(dx * dx + dy * dy);
+            rho = fmaxf(rho, 1e-9f);
+            const float c = (zl - rho) * mp.auxf[0] / rho;
+            g0 = fmaf(c, dx, g0);
+            g1 = fmaf(c, dy, g1);
+        }
+        g[0] = g0; g[1] = g1; g[2] = 0.0f; g[3] = 0.0f;
+    }
+    __device__ static double loglik64(const ModelParams& mp, const float* z, const double* x) {
+        const int nb = (int)mp.p[6];
+        double s = 0.0;
+        for (int l = 0; l < nb; ++l) {
+            const float zl = z[l];
+            if (zl != zl) continue;
+            const double dx = x[0] - mp.p[7 + 2 * l], dy = x[1] - mp.p[8 + 2 * l];
+            const double res = (double)zl - sqrt(dx * dx + dy * dy);
+            s += -0.5 * res * res / mp.p[5] + mp.aux[0];
+        }
+        return s;
+    }
+};
+
+// Unknown association with clutter. p = [dt, q0..q3, r, M, beta, area].
+// aux[0] = log((1-beta)/M) - log(2 pi r), aux[1] = log(beta/area);
+// auxf[0] = 1/r, auxf[1] = aux[0] * log2(e), auxf[2] = aux[1] * log2(e).
+struct ModelClutterCV : CVTransition {
+    static constexpr int KIND = 3, D = 4, DP = 4, DY = 64;
+    __device__ static void grad_loglik(const ModelParams& mp, const float* z, const float* x, float* g) {
+        const int M = (int)mp.p[6];
+        const float rinv = mp.auxf[0];
+        const float c2 = -0.5f * 1.4426950408889634f * rinv;   // log2 units
+        // log2 of each mixture term, then responsibilities by a max-shifted sum
+        float mx = mp.auxf[2];
+        for (int m = 0; m < M; ++m) {
+            const float ex = z[2 * m] - x[0], ey = z[2 * m + 1] - x[1];
+            mx = fmaxf(mx, fmaf(c2, ex * ex + ey * ey, mp.auxf[1]));
+        }
+        float s = fast_exp2(mp.auxf[2] - mx), a0 = 0.0f, a1 = 0.0f;
+        for (int m = 0; m < M; ++m) {
+            const float ex = z[2 * m] - x[0], ey = z[2 * m + 1] - x[1];
+            const float w = fast_exp2(fmaf(c2, ex * ex + ey * ey, mp.auxf[1]) - mx);
+            s += w;
+            a0 = fmaf(w, ex, a0);
+            a1 = fmaf(w, ey, a1);
+        }
+        const float k = rinv / s;
+        g[0] = a0 * k; g[1] = a1 * k; g[2] = 0.0f; g[3] = 0.0f;
+    }
+    __device__ static double loglik64(const ModelParams& mp, const float* z, const double* x) {
+        const int M = (int)mp.p[6];
+        const double rinv = 1.0 / mp.p[5];
+        double mx = mp.aux[1];
+        for (int m = 0; m < M; ++m) {
+            const double ex = (double)z[2 * m] - x[0], ey = (double)z[2 * m + 1] - x[1];
+            mx = fmax(mx, mp.aux[0] - 0.5 * (ex * ex + ey * ey) * rinv);
+        }
+        double s = exp(mp.aux[1] - mx);
+        for (int m = 0; m < M; ++m) {
+            const double ex = (double)z[2 * m] - x[0], ey = (double)z[2 * m + 1] - x[1];
+            s += exp(mp.aux[0] - 0.5 * (ex * ex + ey * ey) * rinv - mx);
+        }
+        return mx + log(s);
+    }
+};
+
+// Planar chain of NL links. p = [dt, nl, r, q_0..q_{2nl-1}, len_0..len_{nl-1}].
+// aux[0] = -log(2 pi r), auxf[0] = 1/r.
+template <int NL>
+struct ModelPlanarArm {
+    static constexpr int KIND = 4, D = 2 * NL, DP = (2 * NL + 3) & ~3, DY = 2;
+    __device__ static double step_const(const ModelParams&, int) { return 0.0; }
+    __device__ static void transition(const ModelParams& mp, double, const float* x, float* f) {
+        const float dt = mp.pf[0];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            f[k] = fmaf(dt, x[NL + k], x[k]);
+            f[NL + k] = x[NL + k];
+        }
+    }
+    __device__ static void transition64(const ModelParams& mp, double, const double* x, double* f) {
+        const double dt = mp.p[0];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            f[k] = x[k] + dt * x[NL + k];
+            f[NL + k] = x[NL + k];
+        }
+    }
+    __device__ static void grad_loglik(const ModelParams& mp, const float* z, const float* x, float* g) {
+        const float* len = mp.pf + 3 + 2 * NL;
+        float lc[NL], ls[NL];
+        float th = 0.0f, ex = 0.0f, ey = 0.0f;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            th += x[l];
+            float s, c;
+            __sincosf(th, &s, &c);
+            lc[l] = len[l] * c;
+            ls[l] = len[l] * s;
+            ex += lc[l];
+            ey += ls[l];
+        }
+        const float rx = (z[0] - ex) * mp.auxf[0], ry = (z[1] - ey) * mp.auxf[0];
+        // d e / d angle_m = sum_{l >= m} len_l (-sin th_l, cos th_l): suffix sums
+        float sx = 0.0f, sy = 0.0f;
+#pragma unroll
+        for (int m = NL - 1; m >= 0; --m) {
+            sx -= ls[m];
+            sy += lc[m];
+            g[m] = fmaf(sx, rx, sy * ry);
+            g[NL + m] = 0.0f;
+        }
+    }
+    __device__ static double loglik64(const ModelParams& mp, const float* z, const double* x) {
+        const double* len = mp.p + 3 + 2 * NL;
+        double th = 0.0, ex = 0.0, ey = 0.0;
+        for (int l = 0; l < NL; ++l) {
+            th += x[l];
+            double s, c;
+            sincos(th, &s, &c);
+            ex += len[l] * c;
+            ey += len[l] * s;
+        }
+        const double rx = (double)z[0] - ex, ry = (double)z[1] - ey;
+        return -0.5 * (rx * rx + ry * ry) / mp.p[2] + mp.aux[0];
+    }
+};
+
+// Linear-Gaussian test model. p = [dt, q0..q3, r].
+// aux[0] = -log(2 pi r), auxf[0] = 1/r.
+struct ModelLinearGauss : CVTransition {
+    static constexpr int KIND = 5, D = 4, DP = 4, DY = 2;
+    __device__ static void grad_loglik(const ModelParams& mp, const float* z, const float* x, float* g) {
+        g[0] = (z[0] - x[0]) * mp.auxf[0];
+        g[1] = (z[1] - x[1]) * mp.auxf[0];
+        g[2] = 0.0f; g[3] = 0.0f;
+    }
+    __device__ static double loglik64(const ModelParams& mp, const float* z, const double* x) {
+        const double ex = (double)z[0] - x[0], ey = (double)z[1] - x[1];
+        return -0.5 * (ex * ex + ey * ey) / mp.p[5] + mp.aux[0];
+    }
+};
+
+}  // namespace smap

@@ -120,13 +120,13 @@ def _cv_step(x, dt, g, q):
 
 
 def make_range_cv(B=1024, T=200, N=256, L=30, step=0.005, seed=2, dropout=(60, 120),
-                  bw_value=1.0, prior=PRIOR_MIXTURE) -> Workload:
+                  bw_value=1.0, prior=PRIOR_MIXTURE, first=0) -> Workload:
     beacons = _rng(2, 999_999).uniform(0.0, 100.0, (3, 2))
     p = range_params(beacons)
     dt, q, r = p[0], p[1], p[5]
     x0 = np.zeros((B, 4)); y = np.zeros((B, T, 3), np.float32); truth = np.zeros((B, T + 1, 4))
     for s in range(B):
-        g = _rng(2, s)
+        g = _rng(2, first + s)
         x = np.concatenate([g.uniform(25.0, 75.0, 2), g.normal(0.0, 1.0, 2)])
         x0[s] = x
         truth[s, 0] = x

@@ -1,0 +1,52 @@
+"""The C-ABI library builds, loads without a GPU, and exports every function
+include/smap.h declares (no compute calls: this runs on CPU-only machines)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    hdr = open(os.path.join(ROOT, "include", "smap.h")).read()
+    pat = re.compile(r"^(?:smap_status|void|int|uint64_t|const char\*)\s+(smap_\w+)\s*\(", re.M)
+    return set(pat.findall(hdr))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    if not __import__("shutil").which("nvcc") and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2312_08684_gb300 import build
+    return build.build()
+
+
+def test_library_exports_every_declared_function(libpath):
+    names = _declared()
+    assert len(names) >= 20
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header(libpath):
+    from paper_2312_08684_gb300 import _binding
+    assert set(_binding.EXPORTS) == _declared()
+    _binding.load()
+    for n in _binding.EXPORTS:
+        assert hasattr(_binding, n), n
+
+
+def test_host_only_calls(libpath):
+    from paper_2312_08684_gb300 import _binding as abi
+    assert abi.smap_status_string(0) == "ok"
+    assert "non-finite" in abi.smap_status_string(6)
+    assert abi.smap_num_variants() >= 1
+    for v in range(abi.smap_num_variants()):
+        ppt, maxt = abi.smap_variant_info(v)
+        assert ppt >= 1 and maxt % 32 == 0
+    with pytest.raises(abi.SmapError):
+        abi.smap_variant_info(99)
+    assert abi.smap_kernel_launches() == 0

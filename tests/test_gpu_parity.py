@@ -1,0 +1,270 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (from the accuracy targets of the method's GPU form):
+  - one SVGD iteration from identical FP32 inputs: max_i |dx_i| / max(1, RMS x)
+    <= 1e-5 (FP32 particles, ex2.approx kernel values);
+  - backpointers and MAP path identical wherever the oracle's score margin
+    (best minus second best) exceeds 1e-6 |score|; scores phi and J in FP64;
+  - final trajectories of whole runs within 1e-3 relative.
+"""
+import numpy as np
+import pytest
+
+from paper_2312_08684_gb300 import Estimator, _binding as abi, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    abi.load()
+
+
+def rel_err(a, b):
+    b = np.asarray(b, np.float64)
+    return float(np.max(np.abs(np.asarray(a, np.float64) - b)) / max(1.0, np.sqrt(np.mean(b * b))))
+
+
+def _oracle_f(m, t, xprev):
+    return np.array([m.transition(t, v) for v in np.asarray(xprev, np.float64)])
+
+
+# ------------------------------------------------------------------ RNG ----
+def test_philox_words_bit_exact(oracle):
+    out = abi.smap_debug_philox(7, 3, 11, 0, 0x1234, 0xBEEF, 4096)
+    for k in range(0, 4096, 97):
+        assert list(out[k]) == list(oracle.philox4x32_10([7 + k, 3, 11, 0], [0x1234, 0xBEEF]))
+    # the known-answer vectors, on the device
+    assert list(abi.smap_debug_philox(0, 0, 0, 0, 0, 0, 1)[0]) == [0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8]
+
+
+@pytest.mark.parametrize("d", [1, 4, 14])
+def test_normals_match_oracle(oracle, d):
+    seed, seq, t = 0xDEADBEEF12345, 5, 17
+    g = abi.smap_debug_normals(seed, seq, t, 0, 2000, d)
+    o = np.array([oracle.normals(seed, seq, t, i, d) for i in range(2000)])
+    # FP32 Box-Muller on the device vs FP64 in the oracle
+    assert np.max(np.abs(g - o) / (1.0 + np.abs(o))) < 2e-6
+
+
+# ------------------------------------------------------- SVGD per iteration ----
+CASES = {
+    "ngm1d": lambda: W.make_ngm1d(B=2, T=6, N=37, L=1),
+    "range": lambda: W.make_range_cv(B=2, T=6, N=70, L=1, dropout=(3, 4)),
+    "clutter": lambda: W.make_clutter_cv(B=2, Tmin=6, Tmax=6, N=45, L=1),
+    "arm": lambda: W.make_planar_arm(B=2, T=6, N=33, L=1),
+    "linear": lambda: W.make_linear_gauss(B=2, T=6, N=29, L=1),
+}
+SPREAD = {"ngm1d": 2.0, "range": 0.3, "clutter": 0.3, "arm": 0.02, "linear": 0.2}
+
+
+def _svgd_case(oracle, name, t, n_iters, prior=0, bw_rule=0, bw_value=1.0, N=None):
+    wl = CASES[name]()
+    if N is not None:
+        wl.N = N
+    wl.prior, wl.bw_rule, wl.bw_value = prior, bw_rule, bw_value
+    m = oracle.Model(wl.kind, wl.params)
+    rng = np.random.default_rng(t * 100 + wl.N)
+    B, N, d = wl.B, wl.N, wl.d
+    if t == 1:
+        xprev = wl.x0[:, None, :].astype(np.float32)
+    else:
+        xprev = (wl.truth[:, t - 1, None, :] + SPREAD[name] * rng.normal(0, 1, (B, N, d))).astype(np.float32)
+    xinit = np.empty((B, N, d), np.float32)
+    fprev = []
+    for b in range(B):
+        f = _oracle_f(m, t, wl.x0[b][None, :] if t == 1 else xprev[b])
+        fprev.append(f)
+        a = f[np.zeros(N, int)] if t == 1 else f
+        xinit[b] = (a + np.sqrt(m.q) * rng.normal(0, 1, (N, d))).astype(np.float32)
+    y = np.ascontiguousarray(wl.y[:, t - 1])
+    with Estimator.from_workload(wl) as est:
+        xg, hg = est.debug_svgd(t, xprev, xinit, y, n_iters)
+    for b in range(B):
+        xo, ho = m.svgd_iters(prior, bw_rule, bw_value, t, y[b].astype(np.float64), fprev[b],
+                              xinit[b].astype(np.float64), n_iters, wl.step)
+        yield b, xg[b], xo, hg[b], ho
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("t", [1, 3])
+def test_one_svgd_iteration_matches_oracle(oracle, name, t):
+    for b, xg, xo, hg, ho in _svgd_case(oracle, name, t, 1):
+        assert np.allclose(hg, ho, rtol=1e-5), (hg, ho)
+        assert rel_err(xg, xo) <= 1e-5, (name, t, b, rel_err(xg, xo))
+
+
+@pytest.mark.parametrize("name", ["range", "linear", "ngm1d"])
+def test_meangrad_prior_matches_oracle(oracle, name):
+    for b, xg, xo, hg, ho in _svgd_case(oracle, name, 3, 1, prior=1):
+        assert rel_err(xg, xo) <= 1e-5
+
+
+@pytest.mark.parametrize("rule,val", [(1, 1.0), (2, 0.5), (0, 3.0), (0, 0.5)])
+def test_bandwidth_rules_match_oracle(oracle, rule, val):
+    for b, xg, xo, hg, ho in _svgd_case(oracle, "range", 3, 3, bw_rule=rule, bw_value=val):
+        assert np.allclose(hg, ho, rtol=1e-5)
+        assert rel_err(xg, xo) <= 3e-5
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 31, 33, 256, 300])
+def test_particle_counts_edge_cases(oracle, N):
+    """N = 1 (gradient ascent), 2, odd / ragged counts around a warp, > 256."""
+    for b, xg, xo, hg, ho in _svgd_case(oracle, "linear", 2, 1, N=N):
+        assert rel_err(xg, xo) <= 1e-5
+
+
+def test_many_iterations_stay_close(oracle):
+    for b, xg, xo, hg, ho in _svgd_case(oracle, "range", 4, 20):
+        assert rel_err(xg, xo) <= 2e-4
+
+
+# --------------------------------------------------------------- Viterbi ----
+def _margins(m, x0, hist, z):
+    """Oracle-side margin (best - second best) / |best| of every psi_t(i)."""
+    T, N, d = hist.shape
+    out = np.full((T, N), np.inf)
+    res = None
+    phi_prev = np.zeros(1)
+    for t in range(1, T + 1):
+        prev = x0[None, :] if t == 1 else hist[t - 2]
+        f = _oracle_f(m, t, prev)
+        psi, phi = m.forward(t, z[t - 1], f, phi_prev, hist[t - 1])
+        if t > 1:
+            for i in range(N):
+                s = np.array([m.logtrans(hist[t - 1, i], f[j]) + phi_prev[j] for j in range(N)])
+                srt = np.sort(s)
+                out[t - 1, i] = (srt[-1] - srt[-2]) / max(1.0, abs(srt[-1]))
+        phi_prev = phi
+    return out
+
+
+@pytest.mark.parametrize("name", ["ngm1d", "range", "clutter", "arm"])
+def test_viterbi_on_identical_particle_sets(oracle, name):
+    wl = {"ngm1d": lambda: W.make_ngm1d(B=2, T=9, N=19),
+          "range": lambda: W.make_range_cv(B=2, T=9, N=35, dropout=(3, 5)),
+          "clutter": lambda: W.make_clutter_cv(B=2, Tmin=9, Tmax=9, N=40),
+          "arm": lambda: W.make_planar_arm(B=2, T=9, N=24)}[name]()
+    m = oracle.Model(wl.kind, wl.params)
+    rng = np.random.default_rng(5)
+    B, T, N, d = wl.B, wl.maxT, wl.N, wl.d
+    hist = (wl.truth[:, 1:, None, :] + SPREAD[name] * rng.normal(0, 1, (B, T, N, d))).astype(np.float32)
+    with Estimator.from_workload(wl) as est:
+        path, J, psi = est.viterbi(hist, wl.y)
+    for b in range(B):
+        ref = oracle.viterbi_sets(wl.kind, wl.params, wl.x0[b], hist[b].astype(np.float64),
+                                  wl.y[b].astype(np.float64))
+        marg = _margins(m, wl.x0[b], hist[b].astype(np.float64), wl.y[b].astype(np.float64))
+        ok = marg > 1e-6
+        assert np.array_equal(psi[b][ok], ref["psi"][ok])
+        assert J[b] == pytest.approx(ref["J"], rel=1e-12, abs=1e-9)
+        assert np.array_equal(path[b], ref["path"].astype(np.float32))
+
+
+# ------------------------------------------------------------ whole runs ----
+def _run_gpu(wl, **kw):
+    with Estimator.from_workload(wl, **kw) as est:
+        path, J = est.run_batch(wl.y, wl.T, wl.Nseq)
+        hist = est.history()
+        psi = est.backpointers()
+    return path, J, hist, psi
+
+
+def _run_oracle(oracle, wl, b):
+    return oracle.run_sequence(wl.kind, wl.params, int(wl.Nseq[b]), wl.L, wl.step, wl.bw_rule,
+                               wl.bw_value, wl.prior, wl.seed, b, wl.x0[b],
+                               wl.y[b, : wl.T[b]].astype(np.float64))
+
+
+def test_full_run_ngm1d_matches_oracle(oracle):
+    """The 1-D growth model at its full size (T=50, N=32, L=50, eps=0.05)."""
+    wl = W.make_ngm1d()
+    path, J, hist, psi = _run_gpu(wl)
+    ref = _run_oracle(oracle, wl, 0)
+    assert rel_err(path[0], ref["path"]) <= 1e-3
+    assert J[0] == pytest.approx(ref["J"], rel=1e-3)
+
+
+@pytest.mark.parametrize("name", ["range", "clutter", "linear"])
+def test_full_run_small_matches_oracle(oracle, name):
+    wl = {"range": lambda: W.make_range_cv(B=3, T=25, N=64, L=10, dropout=(8, 14)),
+          "clutter": lambda: W.make_clutter_cv(B=3, Tmin=10, Tmax=20, N=48, L=10),
+          "linear": lambda: W.make_linear_gauss(B=3, T=15, N=40, L=20)}[name]()
+    path, J, hist, psi = _run_gpu(wl)
+    for b in range(wl.B):
+        T = int(wl.T[b])
+        ref = _run_oracle(oracle, wl, b)
+        assert rel_err(hist[b, :T], ref["hist"]) <= 1e-3
+        assert rel_err(path[b, : T + 1], ref["path"]) <= 1e-3
+        assert J[b] == pytest.approx(ref["J"], rel=1e-3)
+        assert np.all(np.isnan(path[b, T + 1:]))
+
+
+def test_step_loop_equals_batched_graph_run():
+    """Online smap_step calls (with active masks for uneven lengths) give the
+    same bits as the persistent graph-replayed run; replay is deterministic."""
+    wl = W.make_clutter_cv(B=5, Tmin=4, Tmax=9, N=40, L=6)
+    path1, J1, hist1, _ = _run_gpu(wl)
+    with Estimator.from_workload(wl) as est:
+        p2, J2 = est.run_batch(wl.y, wl.T)
+        p3, J3 = est.run_batch(wl.y, wl.T)      # graph replay
+        est.reset()
+        for t in range(wl.maxT):
+            est.step(np.ascontiguousarray(wl.y[:, t]), active=(wl.T > t).astype(np.uint8))
+        p4, J4 = est.map_sequence()
+    for p, J in ((p2, J2), (p3, J3), (p4, J4)):
+        assert np.array_equal(np.nan_to_num(p, nan=1e30), np.nan_to_num(path1, nan=1e30))
+        assert np.array_equal(J, J1)
+
+
+def test_uneven_particle_counts_match_oracle(oracle):
+    wl = W.make_clutter_cv(B=4, Tmin=5, Tmax=12, N=64, L=5, uneven_N=(17, 64))
+    path, J, hist, psi = _run_gpu(wl)
+    for b in range(wl.B):
+        T, N = int(wl.T[b]), int(wl.Nseq[b])
+        ref = _run_oracle(oracle, wl, b)
+        assert rel_err(hist[b, :T, :N], ref["hist"]) <= 1e-3
+        assert J[b] == pytest.approx(ref["J"], rel=1e-3)
+
+
+def test_variants_agree_bitwise():
+    """Every compiled (particles per thread, block) variant runs the same
+    per-particle arithmetic in the same order (mixture prior)."""
+    wl = W.make_range_cv(B=3, T=8, N=64, L=4, dropout=None)
+    outs = []
+    with Estimator.from_workload(wl) as est:
+        for v in range(abi.smap_num_variants()):
+            try:
+                est.set_variant(v)
+            except abi.SmapError:
+                continue
+            outs.append(est.run_batch(wl.y))
+    assert len(outs) >= 2
+    for p, J in outs[1:]:
+        assert np.array_equal(p, outs[0][0]) and np.array_equal(J, outs[0][1])
+
+
+def test_nonfinite_observation_is_reported():
+    wl = W.make_linear_gauss(B=2, T=4, N=16, L=3)
+    y = wl.y.copy()
+    y[1, 2, 0] = np.inf
+    with Estimator.from_workload(wl) as est:
+        with pytest.raises(abi.SmapError) as e:
+            est.step(np.ascontiguousarray(y[:, 2]))
+        assert e.value.status == abi.SMAP_E_NONFINITE
+
+
+def test_bad_arguments_rejected():
+    wl = W.make_linear_gauss(B=2, T=4, N=16, L=3)
+    with pytest.raises(abi.SmapError):
+        Estimator.from_workload(wl, N=0)
+    with pytest.raises(abi.SmapError):
+        Estimator.from_workload(wl, params=wl.params[:-1])
+    with Estimator.from_workload(wl) as est:
+        with pytest.raises(abi.SmapError):
+            est.run_batch(wl.y, T=np.array([5, 1], np.int32))      # > max_T
+        with pytest.raises(abi.SmapError):
+            est.run_batch(wl.y, Nseq=np.array([17, 1], np.int32))  # > N
