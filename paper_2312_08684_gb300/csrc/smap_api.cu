@@ -405,15 +405,15 @@ smap_status copy_outputs(smap_handle* h, float* path, double* J, int on_device) 
 // The device work of one batched run: state reset, the persistent kernel
 // over all sequences, backtracking. Recorded once into a CUDA graph.
 smap_status batch_device_work(smap_handle* h, int v) {
-    SMAP_CUDA(h, cudaEventRecord(h->ev[0], h->stream));
+    SMAP_CUDA(h, cudaEventRecordWithFlags(h->ev[0], h->stream, cudaEventRecordExternal));
     smap_status st = reset_device_state(h);
     if (st) return st;
     st = launch_seq(h, v, h->B, 0, h->y, 0, h->order);
     if (st) return st;
-    SMAP_CUDA(h, cudaEventRecord(h->ev[1], h->stream));
+    SMAP_CUDA(h, cudaEventRecordWithFlags(h->ev[1], h->stream, cudaEventRecordExternal));
     st = launch_backtrack(h);
     if (st) return st;
-    SMAP_CUDA(h, cudaEventRecord(h->ev[2], h->stream));
+    SMAP_CUDA(h, cudaEventRecordWithFlags(h->ev[2], h->stream, cudaEventRecordExternal));
     return SMAP_OK;
 }
 
