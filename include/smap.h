@@ -167,6 +167,31 @@ smap_status smap_viterbi(smap_handle* h, const float* hist, const float* y_all,
                          const int* T_per_seq, const int* N_per_seq, float* path,
                          double* J, uint16_t* psi, int on_device);
 
+/* smap_viterbi for callers that cannot allocate device memory. (The paper has
+ * no counterpart; it exists for the library's callers.) Some callers cannot
+ * call cudaMalloc: a plug-in whose host application owns the device-memory
+ * budget and passes it only input and output buffers, or a control loop that
+ * must not enter the allocator while it runs. A handle allocates, so this
+ * call takes no handle and allocates nothing.
+ *   model / params / n_params  as in smap_config (params: host memory);
+ *   x0 [B][d] FP64, hist [B][T][N][d] FP32, y [B][T][dy] FP32: device inputs;
+ *   path [B][T+1][d] FP32, J [B] FP64: device outputs (as in smap_viterbi).
+ * Its working state (scores, backpointers, transition means, queue, status,
+ * backtracking chain) lives in one static 16 MiB device array of the library,
+ * which every GPU that loads the library holds until the process exits. Sizes
+ * whose working state exceeds 16 MiB (about 2 B T N bytes of backpointers
+ * plus 8 B N (2 + d) bytes of scores and means) are rejected with
+ * SMAP_E_INVAL and a message on stderr. The first call on a device looks up
+ * the array's device address (set-up, once per device, with that device
+ * current); make that first call before any stream capture. The call is
+ * asynchronous on `stream` (cudaStream_t, NULL = legacy default stream) and
+ * clears what it needs at the start of each call; every call shares the
+ * array, so calls that overlap on the GPU (other streams or host threads)
+ * race. A sequence whose scores become non-finite gets J = NaN. */
+smap_status smap_viterbi_noalloc(int model, const double* params, int n_params, int B, int N, int T,
+                                 const double* x0, const float* hist, const float* y, float* path,
+                                 double* J, void* stream);
+
 /* Kernel variant (particles per thread, block size) used by the step kernels.
  * smap_autotune times every compiled variant on the first min(B, sample)
  * sequences for `steps` steps of y_all (layout as in smap_run_batch, host or

@@ -30,6 +30,7 @@ EXPORTS = [
     "smap_autotune", "smap_set_variant", "smap_num_variants", "smap_variant_info",
     "smap_get_variant", "smap_debug_svgd", "smap_debug_philox", "smap_debug_normals",
     "smap_kernel_launches", "smap_status_string", "smap_last_error", "smap_last_kernel_ms",
+    "smap_viterbi_noalloc",
 ]
 
 
@@ -89,6 +90,8 @@ def load():
     L.smap_debug_philox.argtypes = [u32, u32, u32, u32, u32, u32, _I, _VP]
     L.smap_debug_normals.argtypes = [ctypes.c_uint64, u32, u32, u32, _I, _I, _VP]
     L.smap_last_kernel_ms.argtypes = [_VP, _VP, _VP]
+    L.smap_viterbi_noalloc.argtypes = [_I, ctypes.POINTER(ctypes.c_double), _I, _I, _I, _I,
+                                       _VP, _VP, _VP, _VP, _VP, _VP]
     L.smap_kernel_launches.argtypes = []
     L.smap_kernel_launches.restype = ctypes.c_uint64
     L.smap_status_string.argtypes = [_I]
@@ -234,6 +237,22 @@ def smap_viterbi(h, hist, y_all, T_per_seq=None, N_per_seq=None, path=None, J=No
     pj, d5, k5 = _arg(J, np.float64, True)
     ps, d6, k6 = _arg(psi, np.uint16, True)
     _check(load().smap_viterbi(h, ph, py, pt, pn, pp, pj, ps, _same_side(d0, d1, d4, d5, d6)), h)
+
+
+def smap_viterbi_noalloc(model, params, x0, hist, y, path, J, stream=None):
+    """The dynamic programme without device allocation. x0, hist, y, path, J
+    must be CUDA tensors (shapes as in include/smap.h); asynchronous on stream."""
+    params = np.ascontiguousarray(params, dtype=np.float64).ravel()
+    B, T, N, _ = hist.shape
+    ptrs = []
+    for a, dt in ((x0, np.float64), (hist, np.float32), (y, np.float32), (path, np.float32),
+                  (J, np.float64)):
+        p, dev, _ = _arg(a, dt, True)
+        if dev != 1:
+            raise ValueError("smap_viterbi_noalloc takes device tensors only")
+        ptrs.append(p)
+    _check(load().smap_viterbi_noalloc(int(model), params.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       len(params), int(B), int(N), int(T), *ptrs, _stream_ptr(stream)))
 
 
 def smap_autotune(h, y_all, sample, steps):

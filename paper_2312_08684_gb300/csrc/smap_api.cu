@@ -16,7 +16,7 @@
 
 using namespace smap;
 
-namespace {
+namespace smap {
 
 std::atomic<uint64_t> g_launches{0};
 
@@ -175,7 +175,25 @@ bool make_model(int kind, const double* p, int np, ModelParams& mp, std::string&
     return true;
 }
 
-}  // namespace
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Block size of variant v for Nmax particles, or 0 if the variant cannot hold them.
+int variant_threads(int v, int Nmax) {
+    const VariantInfo& vi = kVariants[v];
+    int nt = round_up((Nmax + vi.ppt - 1) / vi.ppt, 32);
+    nt = std::max(nt, 32);
+    return nt <= vi.maxt ? nt : 0;
+}
+
+// Built-in choice of variant for state dimension d and Nmax particles.
+int pick_variant(int d, int Nmax) {
+    if (d >= 8) return variant_threads(1, Nmax) ? 1 : 2;
+    if (Nmax >= 128 && variant_threads(3, Nmax)) return 3;
+    if (variant_threads(0, Nmax)) return 0;
+    return variant_threads(1, Nmax) ? 1 : 2;
+}
+
+}  // namespace smap
 
 struct smap_handle {
     smap_config cfg{};
@@ -244,22 +262,7 @@ smap_status cuda_fail(smap_handle* h, cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
     } while (0)
 
-int round_up(int x, int m) { return (x + m - 1) / m * m; }
-
-// Block size of variant v for Nmax particles, or 0 if the variant cannot hold them.
-int variant_threads(int v, int Nmax) {
-    const VariantInfo& vi = kVariants[v];
-    int nt = round_up((Nmax + vi.ppt - 1) / vi.ppt, 32);
-    nt = std::max(nt, 32);
-    return nt <= vi.maxt ? nt : 0;
-}
-
-int heuristic_variant(const smap_handle* h) {
-    if (h->d >= 8) return variant_threads(1, h->Nmax) ? 1 : 2;
-    if (h->Nmax >= 128 && variant_threads(3, h->Nmax)) return 3;
-    if (variant_threads(0, h->Nmax)) return 0;
-    return variant_threads(1, h->Nmax) ? 1 : 2;
-}
+int heuristic_variant(const smap_handle* h) { return pick_variant(h->d, h->Nmax); }
 
 smap_status configure_kernel(smap_handle* h, const void* fn, size_t smem) {
     if (smem > h->max_smem)

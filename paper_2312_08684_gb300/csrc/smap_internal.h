@@ -1,6 +1,9 @@
 // smap_internal.h -- kernel tables shared by the instantiation units and the ABI.
 #pragma once
 
+#include <atomic>
+#include <string>
+
 #include "smap_common.cuh"
 
 namespace smap {
@@ -24,5 +27,18 @@ ModelKernels kernels_range_cv();
 ModelKernels kernels_clutter_cv();
 ModelKernels kernels_planar_arm7();
 ModelKernels kernels_linear_gauss();
+
+// Shared by the ABI translation units (defined in smap_api.cu).
+extern std::atomic<uint64_t> g_launches;
+const ModelKernels* kernels_for(int kind);
+bool make_model(int kind, const double* p, int np, ModelParams& mp, std::string& err);
+int variant_threads(int v, int Nmax);
+int pick_variant(int d, int Nmax);
+__global__ void backtrack_kernel(int B, int Nmax, int maxT, int d, const int* __restrict__ tcur,
+                                 const int* __restrict__ Nseq, const double* __restrict__ phi,
+                                 const uint16_t* __restrict__ psi, const float* __restrict__ hist,
+                                 const double* __restrict__ x0, const int* __restrict__ status,
+                                 int* __restrict__ idxbuf, float* __restrict__ path,
+                                 double* __restrict__ J);
 
 }  // namespace smap

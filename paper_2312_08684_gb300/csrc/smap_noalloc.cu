@@ -1,0 +1,176 @@
+// smap_noalloc.cu -- smap_viterbi_noalloc: the particle dynamic programme
+// (forward recursion + backtracking over given particle sets) without any
+// device allocation.
+//
+// Some callers cannot call cudaMalloc: a plug-in whose host application owns
+// the whole device-memory budget and hands it only input and output buffers,
+// or a control loop that must never enter the allocator once it runs (an
+// allocation can block or fail). smap_viterbi needs a handle, and a handle
+// allocates its buffers. This entry point keeps its working state (scores,
+// backpointers, transition means, work queue, status words, the backtracking
+// index chain) in one file-scope device array of fixed size instead, which
+// every GPU that loads the library holds until the process exits.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "smap.h"
+#include "smap_internal.h"
+#include "smap_kernels.cuh"
+
+using namespace smap;
+
+namespace {
+
+// Working state of smap_viterbi_noalloc on each device: 16 MiB.
+constexpr size_t kNoallocScratchBytes = size_t(16) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+// Device address of g_noalloc_scratch per device, looked up once per device.
+std::mutex g_noalloc_mu;
+constexpr int kMaxDevices = 256;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Carved {
+    uint16_t* psi;
+    double* phi;
+    double* f64;
+    int *tcur, *Nseq, *Tend, *status, *queue, *idx;
+    float* bwguess;
+    size_t total;
+};
+
+// Sub-buffers of the scratch array (base may be null to size them).
+Carved carve(unsigned char* base, int B, int N, int T, int d, int grid) {
+    Carved c{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) { unsigned char* p = base ? base + off : nullptr; off += a256(bytes); return p; };
+    c.psi = (uint16_t*)take(sizeof(uint16_t) * (size_t)B * T * N);
+    c.phi = (double*)take(sizeof(double) * (size_t)B * N);
+    c.f64 = (double*)take(sizeof(double) * (size_t)grid * N * d);
+    c.tcur = (int*)take(sizeof(int) * (size_t)B);
+    c.Nseq = (int*)take(sizeof(int) * (size_t)B);
+    c.Tend = (int*)take(sizeof(int) * (size_t)B);
+    c.status = (int*)take(sizeof(int) * ((size_t)B + 2));
+    c.queue = (int*)take(sizeof(int) * 4);
+    c.bwguess = (float*)take(sizeof(float) * (size_t)B);
+    c.idx = (int*)take(sizeof(int) * (size_t)B * T);
+    c.total = off;
+    return c;
+}
+
+// Clears what the previous call left in the shared array.
+__global__ void noalloc_init_kernel(int B, int N, int T, int* tcur, int* Nseq, int* Tend, int* status,
+                                    int* queue, float* bwguess) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B + 2; b += gridDim.x * blockDim.x) {
+        status[b] = 0;
+        if (b < B) {
+            tcur[b] = 0;
+            Nseq[b] = N;
+            Tend[b] = T;
+            bwguess[b] = 0.0f;
+        }
+        if (b == 0) queue[0] = 0;
+    }
+}
+
+smap_status reject(const char* msg) {
+    std::fprintf(stderr, "smap_viterbi_noalloc: %s\n", msg);
+    return SMAP_E_INVAL;
+}
+
+}  // namespace
+
+extern "C" smap_status smap_viterbi_noalloc(int model, const double* params, int n_params, int B, int N,
+                                            int T, const double* x0, const float* hist, const float* y,
+                                            float* path, double* J, void* stream) {
+    if (!params || !x0 || !hist || !y || !path || !J) return reject("null pointer argument");
+    if (B < 1 || T < 1 || N < 1 || N > kMaxN) return reject("need B >= 1, T >= 1, 1 <= N <= 4096");
+    const ModelKernels* K = kernels_for(model);
+    if (!K) return reject("unknown model");
+    ModelParams mp;
+    std::string err;
+    if (!make_model(model, params, n_params, mp, err)) return reject(err.c_str());
+    const int d = mp.d;
+    if (d != K->D) return reject("state dimension does not match the compiled model");
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SMAP_E_CUDA;
+    void* base = nullptr;
+    {
+        // set-up, once per device, with that device current
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            cudaError_t e = cudaGetSymbolAddress(&g_noalloc_addr[dev], g_noalloc_scratch);
+            if (e != cudaSuccess) {
+                g_noalloc_addr[dev] = nullptr;
+                std::fprintf(stderr, "smap_viterbi_noalloc: cudaGetSymbolAddress: %s\n", cudaGetErrorString(e));
+                return SMAP_E_CUDA;
+            }
+        }
+        base = g_noalloc_addr[dev];
+    }
+
+    const int v = pick_variant(d, N);
+    const int nt = variant_threads(v, N);
+    const void* fn = K->seq[v];
+    const size_t smem = smem_layout(N, K->DP).total;
+    int smem_optin = 0, sms = 0;
+    if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return SMAP_E_CUDA;
+    if (!nt || smem > (size_t)smem_optin) return reject("N too large for shared memory at this state dimension");
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return SMAP_E_CUDA;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nt, smem) != cudaSuccess || occ < 1)
+        return SMAP_E_CUDA;
+    const int grid = std::max(1, std::min(B, occ * sms));
+
+    const Carved c = carve((unsigned char*)base, B, N, T, d, grid);
+    if (c.total > kNoallocScratchBytes) {
+        char msg[200];
+        std::snprintf(msg, sizeof(msg), "B=%d, N=%d, T=%d need %zu bytes of working state; the maximum is %zu",
+                      B, N, T, c.total, kNoallocScratchBytes);
+        return reject(msg);
+    }
+
+    cudaStream_t st = (cudaStream_t)stream;
+    noalloc_init_kernel<<<(B + 2 + 255) / 256, 256, 0, st>>>(B, N, T, c.tcur, c.Nseq, c.Tend, c.status,
+                                                             c.queue, c.bwguess);
+    SeqArgs a;
+    memset(&a, 0, sizeof(a));
+    a.mp = mp;
+    a.B = B;
+    a.Nmax = N;
+    a.maxT = T;
+    a.mode = 0;
+    a.viterbi_only = 1;
+    a.y = y;
+    a.x0 = x0;
+    a.hist = const_cast<float*>(hist);   // read only when viterbi_only = 1
+    a.psi = c.psi;
+    a.phi = c.phi;
+    a.tcur = c.tcur;
+    a.Nseq = c.Nseq;
+    a.Tend = c.Tend;
+    a.f64 = c.f64;
+    a.bwguess = c.bwguess;
+    a.status = c.status;
+    a.queue = c.queue;
+    void* args[] = {&a};
+    cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, smem, st);
+    backtrack_kernel<<<(B + 3) / 4, 128, 0, st>>>(B, N, T, d, c.tcur, c.Nseq, c.phi, c.psi, hist, x0,
+                                                  c.status, c.idx, path, J);
+    g_launches.fetch_add(3);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        std::fprintf(stderr, "smap_viterbi_noalloc: %s\n", cudaGetErrorString(e));
+        return SMAP_E_CUDA;
+    }
+    return SMAP_OK;
+}
