@@ -231,6 +231,12 @@ smap_status smap_debug_normals(uint64_t seed, uint32_t seq, uint32_t t, uint32_t
  * reset, step kernel, backtracking). Either pointer may be NULL. */
 smap_status smap_last_kernel_ms(smap_handle* h, float* seq_kernel_ms, float* batch_ms);
 
+/* How the exact median of the bandwidth rule was found since the last reset
+ * or batched run, summed over SVGD iterations: counts[0] by the bracket around
+ * the previous median, counts[1] by the log-histogram locate (new step),
+ * counts[2] by the radix-select fallback. Synchronises the stream. */
+smap_status smap_debug_median_stats(smap_handle* h, int* counts);
+
 /* Kernel launches the library has issued since load (its own kernels only). */
 uint64_t smap_kernel_launches(void);
 

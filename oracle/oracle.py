@@ -97,6 +97,8 @@ def lib():
                                           _D, _D, _I, _D, _D]
             L.om_viterbi_sets.argtypes = [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           _D, _D, _D, _I, _D, _D, _D]
+            L.om_viterbi_margins.argtypes = [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             _D, _D, _D, _D]
             L.om_run_batch.argtypes = [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                        ctypes.c_uint64, ctypes.c_int, _I, _D, ctypes.c_int, _I, _D,
@@ -252,6 +254,20 @@ def viterbi_sets(kind, params, x0, hist, z):
     if rc != 0:
         raise ValueError("oracle: viterbi_sets rejected its input")
     return {"psi": psi, "phiT": phiT, "path": path, "J": J.value}
+
+
+def viterbi_margins(kind, params, x0, hist, z):
+    """Relative margin (best - second) / max(1, |best|) of every backpointer, [T][N]."""
+    m = Model(kind, params)
+    hist = _f64(hist); T, N, d = hist.shape
+    z = _f64(z).reshape(-1, m.dy)[:T].copy()
+    x0 = _f64(x0)
+    out = np.empty((T, N))
+    rc = lib().om_viterbi_margins(m.kind, _dp(m.params), len(m.params), N, T, _dp(x0), _dp(hist),
+                                  _dp(z), _dp(out))
+    if rc != 0:
+        raise ValueError("oracle: viterbi_margins rejected its input")
+    return out
 
 
 def run_batch(kind, params, N, L, eps, bw_rule, bw_value, prior, seed, seq_ids, x0, z, T,

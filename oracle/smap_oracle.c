@@ -624,6 +624,45 @@ int om_viterbi_sets(int kind, const double* params, int np, int N, int T,
     return 0;
 }
 
+/* For fixed particle sets: the relative margin of every backpointer,
+ * (best - second best) / max(1, |best|) over j of phi_{t-1}(j) +
+ * log p(x_t^i | x_{t-1}^j), margin[T][N] (t = 1 has a single candidate:
+ * +inf). Used to decide where backpointers are unique to 1e-6. */
+int om_viterbi_margins(int kind, const double* params, int np, int N, int T, const double* x0,
+                       const double* hist, const double* z, double* margin)
+{
+    om_model m;
+    if (om_setup(&m, kind, params, np)) return -1;
+    int d = m.d;
+    double* fprev = (double*)malloc(sizeof(double) * N * d);
+    double* phi_prev = (double*)malloc(sizeof(double) * N);
+    double* phi = (double*)malloc(sizeof(double) * N);
+    int* psi = (int*)malloc(sizeof(int) * N);
+    int Np = 1;
+    phi_prev[0] = 0.0;
+    om_transition(&m, 1, x0, fprev);
+    for (int t = 1; t <= T; ++t) {
+        const double* xt = hist + (size_t)(t - 1) * N * d;
+        if (t > 1)
+            for (int j = 0; j < N; ++j)
+                om_transition(&m, t, hist + ((size_t)(t - 2) * N + j) * d, fprev + (long)j * d);
+        for (int i = 0; i < N; ++i) {
+            double b1 = -INFINITY, b2 = -INFINITY;
+            for (int j = 0; j < Np; ++j) {
+                double v = om_logtrans(&m, xt + (long)i * d, fprev + (long)j * d) + phi_prev[j];
+                if (v > b1) { b2 = b1; b1 = v; } else if (v > b2) { b2 = v; }
+            }
+            double den = fabs(b1) > 1.0 ? fabs(b1) : 1.0;
+            margin[(size_t)(t - 1) * N + i] = (Np == 1) ? INFINITY : (b1 - b2) / den;
+        }
+        om_forward(&m, t, z + (long)(t - 1) * m.dy, fprev, Np, phi_prev, xt, N, psi, phi);
+        memcpy(phi_prev, phi, sizeof(double) * N);
+        Np = N;
+    }
+    free(fprev); free(phi_prev); free(phi); free(psi);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Many sequences on host threads (the CPU baseline runs this).              */
 /* ------------------------------------------------------------------------ */

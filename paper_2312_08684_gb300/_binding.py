@@ -30,7 +30,7 @@ EXPORTS = [
     "smap_autotune", "smap_set_variant", "smap_num_variants", "smap_variant_info",
     "smap_get_variant", "smap_debug_svgd", "smap_debug_philox", "smap_debug_normals",
     "smap_kernel_launches", "smap_status_string", "smap_last_error", "smap_last_kernel_ms",
-    "smap_viterbi_noalloc",
+    "smap_viterbi_noalloc", "smap_debug_median_stats",
 ]
 
 
@@ -90,6 +90,7 @@ def load():
     L.smap_debug_philox.argtypes = [u32, u32, u32, u32, u32, u32, _I, _VP]
     L.smap_debug_normals.argtypes = [ctypes.c_uint64, u32, u32, u32, _I, _I, _VP]
     L.smap_last_kernel_ms.argtypes = [_VP, _VP, _VP]
+    L.smap_debug_median_stats.argtypes = [_VP, _VP]
     L.smap_viterbi_noalloc.argtypes = [_I, ctypes.POINTER(ctypes.c_double), _I, _I, _I, _I,
                                        _VP, _VP, _VP, _VP, _VP, _VP]
     L.smap_kernel_launches.argtypes = []
@@ -317,6 +318,13 @@ def smap_last_kernel_ms(h):
     b = np.zeros(1, np.float32)
     _check(load().smap_last_kernel_ms(h, ctypes.c_void_p(a.ctypes.data), ctypes.c_void_p(b.ctypes.data)), h)
     return float(a[0]), float(b[0])
+
+
+def smap_debug_median_stats(h):
+    """(bracket hits, histogram locates, radix fallbacks) since the last reset / batched run."""
+    out = np.zeros(3, np.int32)
+    _check(load().smap_debug_median_stats(h, ctypes.c_void_p(out.ctypes.data)), h)
+    return tuple(int(v) for v in out)
 
 
 def smap_kernel_launches():

@@ -219,7 +219,7 @@ struct smap_handle {
     double* x0 = nullptr;
     double* f64 = nullptr;
     float* bwguess = nullptr;
-    int* status = nullptr;     // [B + 2]: per-sequence status, then median stats
+    int* status = nullptr;     // [B + kStatusExtra]: per-sequence status, then median stats
     int* queue = nullptr;
     float* y = nullptr;        // [B][maxT][dy]
     float* ystep = nullptr;    // [B][dy]
@@ -391,7 +391,7 @@ smap_status upload_counts(smap_handle* h, const int* T_per_seq, const int* N_per
 
 smap_status reset_device_state(smap_handle* h) {
     SMAP_CUDA(h, cudaMemsetAsync(h->tcur, 0, sizeof(int) * h->B, h->stream));
-    SMAP_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(int) * (h->B + 2), h->stream));
+    SMAP_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(int) * (h->B + kStatusExtra), h->stream));
     SMAP_CUDA(h, cudaMemsetAsync(h->bwguess, 0, sizeof(float) * h->B, h->stream));
     return SMAP_OK;
 }
@@ -441,6 +441,15 @@ const char* smap_status_string(smap_status s) {
 const char* smap_last_error(const smap_handle* h) { return h ? h->err.c_str() : "null handle"; }
 
 uint64_t smap_kernel_launches(void) { return g_launches.load(); }
+
+smap_status smap_debug_median_stats(smap_handle* h, int* counts) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    if (!counts) return fail(h, SMAP_E_INVAL, "null output");
+    SMAP_CUDA(h, cudaMemcpyAsync(counts, h->status + h->B, sizeof(int) * 3, cudaMemcpyDeviceToHost, h->stream));
+    SMAP_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SMAP_OK;
+}
 
 smap_status smap_last_kernel_ms(smap_handle* h, float* seq_ms, float* batch_ms) {
     smap_status st = check_usable(h);
@@ -542,7 +551,7 @@ smap_status smap_create(const smap_config* cfg, smap_handle** out) {
         {(void**)&h->x0, sizeof(double) * B * d},
         {(void**)&h->f64, sizeof(double) * B * N * d},
         {(void**)&h->bwguess, sizeof(float) * B},
-        {(void**)&h->status, sizeof(int) * (B + 2)},
+        {(void**)&h->status, sizeof(int) * (B + kStatusExtra)},
         {(void**)&h->queue, sizeof(int) * 4},
         {(void**)&h->y, sizeof(float) * B * T * dy},
         {(void**)&h->ystep, sizeof(float) * B * dy},

@@ -11,6 +11,7 @@ constexpr int kMaxParams = 128;  // model parameter vector length
 constexpr int kMaxDy = 64;       // largest observation dimension
 constexpr int kCandCap = 2048;   // median bracket candidates kept in shared memory
 constexpr int kMaxN = 4096;      // particles per sequence (backpointers are uint16)
+constexpr int kStatusExtra = 4;  // counters after the B per-sequence status words
 
 // Model constants, passed by value in the kernel parameters (constant bank).
 struct ModelParams {

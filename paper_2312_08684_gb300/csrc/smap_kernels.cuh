@@ -2,8 +2,8 @@
 //
 // One CTA owns one sequence at a time and runs its time steps with the
 // particle sets resident in shared memory:
-//   a1  f_j = f_t(x_{t-1}^j) for the previous set (FP32 for the SVGD prior,
-//       FP64 for the recursion), centred and scaled by Q^-1/2;
+//   a1  f_j = f_t(x_{t-1}^j) for the previous set (FP64, kept for the
+//       recursion; FP32 copies centred and scaled by Q^-1/2 for the prior);
 //   a2  x_t^{i,(0)} = f_t(x_{t-1}^i) + Q^{1/2} xi_i (Philox noise);
 //   a3  h = s * med / log N from an exact median of the squared distances;
 //   a4  g_k = grad log p(z_t | x_k) + grad log prior(x_k) (mixture over j);
@@ -12,12 +12,22 @@
 //   a7  psi_t(i), phi_t(i) of Eq. forward_recursion with FP64 scores;
 // then stores x_t and psi_t to HBM. Sequences are taken from a device work
 // queue (persistent CTAs), so uneven lengths and particle counts balance.
+//
+// During the SVGD iterations the particles are held centred (on c = f_t of
+// the first previous particle) and scaled by sqrt(log2(e)/h), so that
+// kappa_ik = 2^-|x^_i - x^_k|^2 costs one ex2 and no multiply; the prior works
+// in coordinates scaled by Q^-1/2 sqrt(log2(e)/2), where the mixture logit of
+// j is -|x~ - f~_j|^2 in log2 units.
 #pragma once
 
 #include "smap_common.cuh"
 #include "smap_models.cuh"
 
 namespace smap {
+
+constexpr float kL2E = 1.4426950408889634f;    // log2(e)
+constexpr float kKm = 0.84932180028801907f;    // sqrt(log2(e) / 2)
+constexpr float kLam = 1.3862943611198906f;    // 1 / kKm^2 = 2 ln 2
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -43,10 +53,10 @@ __host__ __device__ inline SmemLayout smem_layout(int Nmax, int DP) {
 
 struct Sm {
     double* phis;   // phi_{t-1}(j), j < Np
-    float* xs;      // particles [N][DP]
+    float* xs;      // particles [N][DP] (absolute, or centred+scaled inside SVGD)
     float* gs;      // scores [N][DP]; later (A+, A-) pairs of the recursion screen
-    float* fs;      // (f_t(x_{t-1}^j) - c) * Q^-1/2, [Np][DP]
-    uint32_t* cand; // median candidates / radix histogram
+    float* fs;      // (f_t(x_{t-1}^j) - c) Q^-1/2 kKm, [Np][DP]
+    uint32_t* cand; // median candidates / histograms
     float* zs;      // observation z_t
     double* redd;   // reduction scratch (aliases redi / redf)
     int* redi;
@@ -72,6 +82,31 @@ __device__ inline Sm bind_smem(unsigned char* base, int Nmax, int DP) {
     return s;
 }
 
+// Row i of a [*][DP] shared array: 128-bit loads when DP is a multiple of 4.
+template <int D, int DP>
+__device__ __forceinline__ void load_row(const float* base, int i, float* r) {
+    if constexpr (DP % 4 == 0) {
+        const float4* p = reinterpret_cast<const float4*>(base + i * DP);
+#pragma unroll
+        for (int q = 0; q < DP / 4; ++q) {
+            const float4 v = p[q];
+            if (4 * q + 0 < D) r[4 * q + 0] = v.x;
+            if (4 * q + 1 < D) r[4 * q + 1] = v.y;
+            if (4 * q + 2 < D) r[4 * q + 2] = v.z;
+            if (4 * q + 3 < D) r[4 * q + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < D; ++c) r[c] = base[i * DP + c];
+    }
+}
+
+template <int D, int DP>
+__device__ __forceinline__ void store_row(float* base, int i, const float* r) {
+#pragma unroll
+    for (int c = 0; c < DP; ++c) base[i * DP + c] = c < D ? r[c] : 0.0f;
+}
+
 template <int D>
 __device__ __forceinline__ float sqdist(const float* a, const float* b) {
     float s = 0.0f;
@@ -81,12 +116,6 @@ __device__ __forceinline__ float sqdist(const float* a, const float* b) {
         s = fmaf(e, e, s);
     }
     return s;
-}
-
-template <int D, int DP>
-__device__ __forceinline__ void load_row(const float* xs, int i, float* r) {
-#pragma unroll
-    for (int c = 0; c < D; ++c) r[c] = xs[i * DP + c];
 }
 
 // ---------------------------------------------------------------------------
@@ -113,26 +142,36 @@ __device__ __forceinline__ void for_each_pair(const float* xs, int N, F& f) {
         if (m0 < e1) {
             float xr[D];
             load_row<D, DP>(xs, r, xr);
-            for (int m = m0; m < e1; ++m) f(sqdist<D>(xr, xs + (r + 1 + m) * DP));
+#pragma unroll 4
+            for (int m = m0; m < e1; ++m) {
+                float xk[D];
+                load_row<D, DP>(xs, r + 1 + m, xk);
+                f(sqdist<D>(xr, xk));
+            }
         }
         const int b2 = max(m0, len1);
         if (b2 < m1) {
             float xr[D];
             load_row<D, DP>(xs, r2, xr);
-            for (int m = b2; m < m1; ++m) f(sqdist<D>(xr, xs + (r2 + 1 + (m - len1)) * DP));
+#pragma unroll 4
+            for (int m = b2; m < m1; ++m) {
+                float xk[D];
+                load_row<D, DP>(xs, r2 + 1 + (m - len1), xk);
+                f(sqdist<D>(xr, xk));
+            }
         }
     }
 }
 
+// Counts keys below lo and collects the keys in [lo, hi].
 struct BracketCount {
-    uint32_t lo, hi;
+    float lo, hi;
     int nlo;
     uint32_t* cand;
     int* ncand;
     __device__ __forceinline__ void operator()(float v) {
-        const uint32_t key = __float_as_uint(v);
-        nlo += key < lo;
-        const bool in = (key >= lo) & (key <= hi);
+        nlo += v < lo;
+        const bool in = (v >= lo) & (v <= hi);
         const unsigned act = __activemask();
         const unsigned bal = __ballot_sync(act, in);
         if (bal) {
@@ -142,9 +181,22 @@ struct BracketCount {
             base = __shfl_sync(act, base, leader);
             if (in) {
                 const int idx = base + __popc(bal & ((1u << lane_id()) - 1u));
-                if (idx < kCandCap) cand[idx] = key;
+                if (idx < kCandCap) cand[idx] = __float_as_uint(v);
             }
         }
+    }
+};
+
+// 256-bin histogram of the key bits >> 18 (1/32 octave per bin), centred on a
+// guess; the two end bins collect the tails.
+struct LogHist {
+    int base;
+    int* hist;
+    __device__ __forceinline__ void operator()(float v) {
+        const int bin = min(max((int)(__float_as_uint(v) >> 18) - base, 0), 255);
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, bin);
+        if ((int)lane_id() == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
     }
 };
 
@@ -208,61 +260,137 @@ __device__ inline void bitonic_sort(uint32_t* c, int n2) {
     }
 }
 
-// Median of the squared pairwise distances. A bracket around the previous
-// median is counted in one pass and its members sorted; if the bracket misses
-// the middle ranks or overflows, an exact radix select decides. guess / w
-// (bracket half-width, relative) carry over between calls. stats (may be
-// null): [0] bracket hits, [1] radix fallbacks.
+// One bracket pass over all pairs: on success (the middle ranks fall inside
+// [lo, hi] and at most kCandCap keys do) v1, v2 are the keys of ranks r1, r2.
 template <int D, int DP>
-__device__ float median_sqdist(const Sm& s, int N, float& guess, float& w, bool& have_guess,
-                               int* stats) {
+__device__ bool bracket_pass(const Sm& s, int N, float lo, float hi, int r1, int r2, uint32_t& v1,
+                             uint32_t& v2, int& nc_out) {
+    if (threadIdx.x == 0) *s.ncand = 0;
+    __syncthreads();
+    BracketCount f{lo, hi, 0, s.cand, s.ncand};
+    for_each_pair<D, DP>(s.xs, N, f);
+    const int nlo = block_sum_int(f.nlo, s.redi);   // ends with a barrier
+    const int nc = *s.ncand;
+    nc_out = nc;
+    bool ok = nlo <= r1 && r2 < nlo + nc && nc <= kCandCap;
+    if (ok) {
+        int n2 = 1;
+        while (n2 < nc) n2 <<= 1;
+        for (int i = nc + threadIdx.x; i < n2; i += blockDim.x) s.cand[i] = 0xFFFFFFFFu;
+        __syncthreads();
+        bitonic_sort(s.cand, n2);
+        v1 = s.cand[r1 - nlo];
+        v2 = s.cand[r2 - nlo];
+    }
+    __syncthreads();
+    return ok;
+}
+
+// Median state carried across iterations and steps (uniform over the block).
+struct MedState {
+    float med;     // last median (absolute units)
+    float trend;   // ratio of the last two medians
+    float w;       // bracket half-width, relative
+    int have;      // med is valid
+    int fresh;     // the set changed beyond one SVGD update (new step)
+};
+
+// Median of the squared pairwise distances of the particles in xs, whose
+// coordinates are scaled by sqrt(s2) (so scaled distances = s2 * true ones).
+// Returns the median in true units. Path: a tight bracket around the
+// extrapolated previous median (usual case); at a new step, a 256-bin
+// histogram over +-4 octaves locates the bracket first; an exact radix
+// select is the last resort. stats (may be null): [0] bracket hits,
+// [1] histogram locates, [2] radix fallbacks.
+template <int D, int DP>
+__device__ float median_sqdist(const Sm& s, int N, float s2, float q_extra, MedState& st, int* stats) {
     const int P = N * (N - 1) / 2;
     const int r1 = (P & 1) ? (P - 1) / 2 : P / 2 - 1;
     const int r2 = (P & 1) ? r1 : P / 2;
     uint32_t v1 = 0, v2 = 0;
+    int nc = 0, path = 2;
     bool done = false;
-    if (have_guess && guess > 0.0f && isfinite(guess)) {
-        if (threadIdx.x == 0) *s.ncand = 0;
-        __syncthreads();
-        BracketCount f{__float_as_uint(guess * (1.0f - w)), __float_as_uint(guess * (1.0f + w)), 0,
-                       s.cand, s.ncand};
-        for_each_pair<D, DP>(s.xs, N, f);
-        const int nlo = block_sum_int(f.nlo, s.redi);   // ends with a barrier
-        const int nc = *s.ncand;
-        if (nlo <= r1 && r2 < nlo + nc && nc <= kCandCap) {
-            int n2 = 1;
-            while (n2 < nc) n2 <<= 1;
-            for (int i = nc + threadIdx.x; i < n2; i += blockDim.x) s.cand[i] = 0xFFFFFFFFu;
-            __syncthreads();
-            bitonic_sort(s.cand, n2);
-            v1 = s.cand[r1 - nlo];
-            v2 = s.cand[r2 - nlo];
-            done = true;
-            if (nc * 8 < kCandCap) w = fmaxf(w * 0.7f, 1e-4f);
-            else if (nc * 2 > kCandCap) w *= 0.5f;
-        } else if (nc > kCandCap) {
-            w *= 0.3f;
+    if (st.have && !st.fresh) {
+        const float g = st.med * st.trend * s2;
+        done = bracket_pass<D, DP>(s, N, g * (1.0f - st.w), g * (1.0f + st.w), r1, r2, v1, v2, nc);
+        if (done) {
+            path = 0;
+            if (nc > 512) st.w *= 0.6f;
+            else if (nc < 48) st.w = fminf(st.w * 1.5f, 0.05f);
         } else {
-            w = fminf(w * 3.0f, 1.0f);
+            st.w = fminf(st.w * 2.0f, 0.05f);
         }
-        __syncthreads();
+    }
+    if (!done) {
+        // locate the middle ranks in a 256-bin log histogram around a guess
+        float g;
+        if (st.have) {
+            g = (st.med + q_extra) * s2;
+        } else {
+            // crude guess: mean of a few pair distances
+            float a = 0.0f;
+            if (threadIdx.x < 32) {
+                const int i = (threadIdx.x * 7) % N, k = (threadIdx.x * 13 + N / 2 + 1) % N;
+                float xi[D], xk[D];
+                load_row<D, DP>(s.xs, i, xi);
+                load_row<D, DP>(s.xs, k, xk);
+                a = sqdist<D>(xi, xk);
+            }
+            a = warp_sum_f(a);
+            if (threadIdx.x == 0) s.redf[38] = a / 32.0f;
+            __syncthreads();
+            g = s.redf[38];
+            __syncthreads();
+        }
+        if (g > 0.0f && isfinite(g)) {
+            int* hist = reinterpret_cast<int*>(s.cand);
+            for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+            __syncthreads();
+            LogHist f{(int)(__float_as_uint(g) >> 18) - 128, hist};
+            for_each_pair<D, DP>(s.xs, N, f);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int cum = 0, b1 = -1, b2 = -1;
+                for (int bin = 0; bin < 256; ++bin) {
+                    const int c = hist[bin];
+                    if (b1 < 0 && cum + c > r1) b1 = bin;
+                    if (b2 < 0 && cum + c > r2) { b2 = bin; break; }
+                    cum += c;
+                }
+                s.redi[36] = b1;
+                s.redi[37] = b2;
+            }
+            __syncthreads();
+            const int b1 = s.redi[36], b2 = s.redi[37];
+            __syncthreads();
+            if (b1 > 0 && b2 < 255 && b2 >= b1 && f.base + b1 >= 0) {
+                const uint32_t lo = (uint32_t)(f.base + b1) << 18;
+                const uint32_t hi = ((uint32_t)(f.base + b2 + 1) << 18) - 1u;
+                done = bracket_pass<D, DP>(s, N, __uint_as_float(lo), __uint_as_float(hi), r1, r2, v1, v2, nc);
+                if (done) path = 1;
+            }
+        }
     }
     if (!done) {
         v1 = radix_select<D, DP>(s, N, r1);
         v2 = (r2 == r1) ? v1 : radix_select<D, DP>(s, N, r2);
     }
-    if (stats && threadIdx.x == 0) atomicAdd(&stats[done ? 0 : 1], 1);
-    const float med = 0.5f * (__uint_as_float(v1) + __uint_as_float(v2));
-    guess = med;
-    have_guess = true;
+    if (stats && threadIdx.x == 0) atomicAdd(&stats[path], 1);
+    const float med = 0.5f * (__uint_as_float(v1) + __uint_as_float(v2)) / s2;
+    if (st.have && !st.fresh && st.med > 0.0f) st.trend = fminf(fmaxf(med / st.med, 0.8f), 1.25f);
+    else st.trend = 1.0f;
+    if (st.fresh || !st.have) st.w = 0.004f;
+    st.med = med;
+    st.have = 1;
+    st.fresh = 0;
     return med;
 }
 
 // ---------------------------------------------------------------------------
 // a1/a2: transition means of the previous set and the initial particles.
 // On return (after a barrier): fs, misc (centre, fs mean), zs, f64 are set
-// and xs holds the initial particles of step t. first = the previous set is
-// {x_0^true} (taken in FP64 from x0).
+// and xs holds the initial particles of step t (absolute FP32). first = the
+// previous set is {x_0^true} (taken in FP64 from x0).
 // ---------------------------------------------------------------------------
 template <class M, int PPT>
 __device__ void prepare_step(const ModelParams& mp, const Sm& s, int t, int N, int Np, bool first,
@@ -279,7 +407,10 @@ __device__ void prepare_step(const ModelParams& mp, const Sm& s, int t, int N, i
     float cf[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) cf[c] = (float)f0[c];
-    if (tid < D) s.misc[tid] = cf[tid];
+    if (tid == 0) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) s.misc[c] = cf[c];
+    }
     __syncthreads();
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
@@ -295,13 +426,13 @@ __device__ void prepare_step(const ModelParams& mp, const Sm& s, int t, int N, i
                 for (int c = 0; c < D; ++c) xd[c] = (double)s.xs[i * DP + c];
                 M::transition64(mp, sc, xd, fd);
             }
+            float fr[D];
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 f64[(size_t)i * D + c] = fd[c];
-                s.fs[i * DP + c] = (float)((fd[c] - (double)cf[c]) * mp.sqrt_qinv[c]);
+                fr[c] = (float)((fd[c] - (double)cf[c]) * (mp.sqrt_qinv[c] * (double)kKm));
             }
-#pragma unroll
-            for (int c = D; c < DP; ++c) s.fs[i * DP + c] = 0.0f;
+            store_row<D, DP>(s.fs, i, fr);
         }
         if (i < N) {
             float xi[D];
@@ -315,10 +446,7 @@ __device__ void prepare_step(const ModelParams& mp, const Sm& s, int t, int N, i
 #pragma unroll
                 for (int c = 0; c < D; ++c) xi[c] = (float)(fa[c] + mp.sqrt_q[c] * (double)z[c]);
             }
-#pragma unroll
-            for (int c = 0; c < D; ++c) s.xs[i * DP + c] = xi[c];
-#pragma unroll
-            for (int c = D; c < DP; ++c) s.xs[i * DP + c] = 0.0f;
+            store_row<D, DP>(s.xs, i, xi);
         }
     }
     if (prior == 1) {   // MEANGRAD needs mean_j fs_j
@@ -334,55 +462,87 @@ __device__ void prepare_step(const ModelParams& mp, const Sm& s, int t, int N, i
 }
 
 // ---------------------------------------------------------------------------
-// a4: scores g_i = grad log p(z_t | x_i) + grad log prior(x_i) -> gs.
+// a4: scores g_i = grad log p(z_t | x_i) + grad log prior(x_i) -> gs, for the
+// block's particles held as x^ = (x - c) * sc in xs; each particle is first
+// rescaled by `rescale` (the new kernel scale over the old) and written back.
 // ---------------------------------------------------------------------------
 template <class M, int PPT>
-__device__ __forceinline__ void compute_scores(const ModelParams& mp, const Sm& s, int N, int Np,
-                                               int prior) {
+__device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const Sm& s, int N, int Np,
+                                                  int prior, float rescale, float inv_sc) {
     constexpr int D = M::D, DP = M::DP;
     const int tid = threadIdx.x, NT = blockDim.x;
-    const float kL2E = 1.4426950408889634f;
-    float xt[PPT][D], A[PPT][D], S[PPT], Mx[PPT];
-    float sq[D], cf[D];
+    float xt[PPT][D], A[PPT][D], S[PPT], Mref[PPT];
+    float cf[D], qk[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) { sq[c] = mp.sqrt_qinv_f[c]; cf[c] = s.misc[c]; }
+    for (int c = 0; c < D; ++c) {
+        cf[c] = s.misc[c];
+        qk[c] = mp.sqrt_qinv_f[c] * kKm * inv_sc;   // x^ -> mixture coordinates
+    }
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
-        const int i = min(tid + p * NT, N - 1);
+        const int i = tid + p * NT;
+        const int ii = min(i, N - 1);
+        float xh[D];
+        load_row<D, DP>(s.xs, ii, xh);
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            xt[p][c] = (s.xs[i * DP + c] - cf[c]) * sq[c];
+            xh[c] *= rescale;
+            xt[p][c] = xh[c] * qk[c];
             A[p][c] = 0.0f;
         }
+        if (i < N) store_row<D, DP>(s.xs, i, xh);
         S[p] = 0.0f;
-        Mx[p] = -INFINITY;
+        // reference logit: the particle's own parent in the previous set
+        float fr[D];
+        load_row<D, DP>(s.fs, Np == 1 ? 0 : min(ii, Np - 1), fr);
+        Mref[p] = -sqdist<D>(xt[p], fr);
     }
     if (prior == 0) {
-        // mixture: responsibilities w_ij = softmax_j(-1/2 |x_i - f_j|^2_{Q^-1}),
-        // accumulated with a running maximum (log2 units)
+        // mixture responsibilities w_ij = 2^-(|x~_i - f~_j|^2 + Mref) / sum:
+        // the parent's term is 1, so the sum is >= 1; a sum above 2^100 (a
+        // far better component than the parent) is redone with the true max
         for (int j = 0; j < Np; ++j) {
             float fj[D];
             load_row<D, DP>(s.fs, j, fj);
 #pragma unroll
             for (int p = 0; p < PPT; ++p) {
-                float diff[D], m = 0.0f;
+                float diff[D], m = Mref[p];
 #pragma unroll
                 for (int c = 0; c < D; ++c) {
                     diff[c] = xt[p][c] - fj[c];
                     m = fmaf(diff[c], diff[c], m);
                 }
-                const float lg = m * (-0.5f * kL2E);
-                if (lg > Mx[p]) {
-                    const float r = fast_exp2(Mx[p] - lg);
-                    S[p] *= r;
-#pragma unroll
-                    for (int c = 0; c < D; ++c) A[p][c] *= r;
-                    Mx[p] = lg;
-                }
-                const float e = fast_exp2(lg - Mx[p]);
+                const float e = fast_exp2(-m);
                 S[p] += e;
 #pragma unroll
                 for (int c = 0; c < D; ++c) A[p][c] = fmaf(e, diff[c], A[p][c]);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            if (!(S[p] <= 1.2676506e30f)) {   // 2^100, or NaN
+                float mn = INFINITY;
+                for (int j = 0; j < Np; ++j) {
+                    float fj[D];
+                    load_row<D, DP>(s.fs, j, fj);
+                    mn = fminf(mn, sqdist<D>(xt[p], fj));
+                }
+                S[p] = 0.0f;
+#pragma unroll
+                for (int c = 0; c < D; ++c) A[p][c] = 0.0f;
+                for (int j = 0; j < Np; ++j) {
+                    float fj[D], diff[D], m = -mn;
+                    load_row<D, DP>(s.fs, j, fj);
+#pragma unroll
+                    for (int c = 0; c < D; ++c) {
+                        diff[c] = xt[p][c] - fj[c];
+                        m = fmaf(diff[c], diff[c], m);
+                    }
+                    const float e = fast_exp2(-m);
+                    S[p] += e;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) A[p][c] = fmaf(e, diff[c], A[p][c]);
+                }
             }
         }
     }
@@ -391,44 +551,46 @@ __device__ __forceinline__ void compute_scores(const ModelParams& mp, const Sm& 
         const int i = tid + p * NT;
         if (i >= N) continue;
         float x[D], g[D];
+        float xh[D];
+        load_row<D, DP>(s.xs, i, xh);
 #pragma unroll
-        for (int c = 0; c < D; ++c) x[c] = s.xs[i * DP + c];
+        for (int c = 0; c < D; ++c) x[c] = fmaf(xh[c], inv_sc, cf[c]);
         M::grad_loglik(mp, s.zs, x, g);
+        // Q^-1 (f - x) = -(Q^-1/2 / kKm) (x~ - f~)
         if (prior == 0) {
             const float inv = 1.0f / S[p];
 #pragma unroll
-            for (int c = 0; c < D; ++c) g[c] -= sq[c] * A[p][c] * inv;
+            for (int c = 0; c < D; ++c) g[c] -= mp.sqrt_qinv_f[c] * (1.0f / kKm) * A[p][c] * inv;
         } else {
 #pragma unroll
-            for (int c = 0; c < D; ++c) g[c] -= sq[c] * (xt[p][c] - s.misc[16 + c]);
+            for (int c = 0; c < D; ++c)
+                g[c] -= mp.sqrt_qinv_f[c] * (1.0f / kKm) * (xt[p][c] - s.misc[16 + c]);
         }
-#pragma unroll
-        for (int c = 0; c < D; ++c) s.gs[i * DP + c] = g[c];
-#pragma unroll
-        for (int c = D; c < DP; ++c) s.gs[i * DP + c] = 0.0f;
+        store_row<D, DP>(s.gs, i, g);
     }
 }
 
 // ---------------------------------------------------------------------------
-// a5: one SVGD update of the block's particles (Eq. svgd_iterate).
+// a5: one SVGD update (Eq. svgd_iterate) in the scaled coordinates:
+// kappa_ik = 2^-|x^_i - x^_k|^2, x^_i += A sum_k kappa g_k + Bc sum_k kappa (x^_i - x^_k)
+// with A = sc eps / N and Bc = 2 eps / (N h).
 // ---------------------------------------------------------------------------
 template <class M, int PPT>
-__device__ __forceinline__ void rbf_update(const Sm& s, int N, float h, float eps) {
+__device__ __forceinline__ void rbf_update(const Sm& s, int N, float A, float Bc) {
     constexpr int D = M::D, DP = M::DP;
     const int tid = threadIdx.x, NT = blockDim.x;
-    const float c2 = -1.4426950408889634f / h;
-    const float twoh = 2.0f / h;
     float xi[PPT][D], Sg[PPT][D], Sd[PPT][D];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         const int i = min(tid + p * NT, N - 1);
+        load_row<D, DP>(s.xs, i, xi[p]);
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            xi[p][c] = s.xs[i * DP + c];
             Sg[p][c] = 0.0f;
             Sd[p][c] = 0.0f;
         }
     }
+#pragma unroll 2
     for (int k = 0; k < N; ++k) {
         float xk[D], gk[D];
         load_row<D, DP>(s.xs, k, xk);
@@ -441,7 +603,7 @@ __device__ __forceinline__ void rbf_update(const Sm& s, int N, float h, float ep
                 diff[c] = xi[p][c] - xk[c];
                 m = fmaf(diff[c], diff[c], m);
             }
-            const float kap = fast_exp2(m * c2);
+            const float kap = fast_exp2(-m);
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 Sg[p][c] = fmaf(kap, gk[c], Sg[p][c]);
@@ -449,23 +611,44 @@ __device__ __forceinline__ void rbf_update(const Sm& s, int N, float h, float ep
             }
         }
     }
-    const float sc = eps / (float)N;
     __syncthreads();   // every thread is done reading xs / gs
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         const int i = tid + p * NT;
         if (i >= N) continue;
+        float xn[D];
 #pragma unroll
-        for (int c = 0; c < D; ++c) s.xs[i * DP + c] = fmaf(sc, fmaf(twoh, Sd[p][c], Sg[p][c]), xi[p][c]);
+        for (int c = 0; c < D; ++c) xn[c] = fmaf(A, Sg[p][c], fmaf(Bc, Sd[p][c], xi[p][c]));
+        store_row<D, DP>(s.xs, i, xn);
     }
     __syncthreads();
 }
 
-// a3..a6: L iterations. hout (may be null) receives h per iteration.
+// a3..a6: L iterations on the absolute particles in xs (left absolute on
+// return). hout (may be null) receives h per iteration.
 template <class M, int PPT>
 __device__ void svgd_iterations(const ModelParams& mp, const Sm& s, int N, int Np, int L, float eps,
-                                int bw_rule, float bw_value, int prior, float& guess, float& w,
-                                bool& have_guess, float* hout, int* stats) {
+                                int bw_rule, float bw_value, int prior, MedState& st, float q_extra,
+                                float* hout, int* stats) {
+    constexpr int D = M::D, DP = M::DP;
+    if (L <= 0) return;
+    const int tid = threadIdx.x, NT = blockDim.x;
+    float cf[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) cf[c] = s.misc[c];
+    // centre (scale 1)
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        const int i = tid + p * NT;
+        if (i >= N) continue;
+        float xr[D];
+        load_row<D, DP>(s.xs, i, xr);
+#pragma unroll
+        for (int c = 0; c < D; ++c) xr[c] -= cf[c];
+        store_row<D, DP>(s.xs, i, xr);
+    }
+    __syncthreads();
+    float sc = 1.0f;   // current scale of xs
     float h = 1.0f;
     for (int l = 0; l < L; ++l) {
         if (bw_rule == 2) {
@@ -474,23 +657,52 @@ __device__ void svgd_iterations(const ModelParams& mp, const Sm& s, int N, int N
             if (N < 2) {
                 h = 1.0f;
             } else {
-                if (l == 0) w = fmaxf(w, 0.25f);
-                const float med = median_sqdist<M::D, M::DP>(s, N, guess, w, have_guess, stats);
+                const float med = median_sqdist<D, DP>(s, N, sc * sc, q_extra, st, stats);
                 h = (med > 0.0f) ? bw_value * med / logf((float)N) : 1.0f;
             }
         }
-        if (hout && threadIdx.x == 0) hout[l] = h;
-        compute_scores<M, PPT>(mp, s, N, Np, prior);
+        if (hout && tid == 0) hout[l] = h;
+        const float sc_new = sqrtf(kL2E / h);
+        rescale_and_score<M, PPT>(mp, s, N, Np, prior, sc_new / sc, 1.0f / sc_new);
+        sc = sc_new;
         __syncthreads();
-        rbf_update<M, PPT>(s, N, h, eps);
+        const float A = sc * eps / (float)N;
+        const float Bc = 2.0f * eps / ((float)N * h);
+        rbf_update<M, PPT>(s, N, A, Bc);
     }
+    // back to absolute coordinates
+    const float inv = 1.0f / sc;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        const int i = tid + p * NT;
+        if (i >= N) continue;
+        float xr[D];
+        load_row<D, DP>(s.xs, i, xr);
+#pragma unroll
+        for (int c = 0; c < D; ++c) xr[c] = fmaf(xr[c], inv, cf[c]);
+        store_row<D, DP>(s.xs, i, xr);
+    }
+    __syncthreads();
+}
+
+// |x - f|^2_{Q^-1} in FP64 for an FP32 particle x and an FP64 mean f.
+template <int D>
+__device__ __forceinline__ double trans_m64(const ModelParams& mp, const float* x, const double* f) {
+    double m64 = 0.0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        const double e = (double)x[c] - f[c];
+        m64 += e * e * mp.qinv[c];
+    }
+    return m64;
 }
 
 // ---------------------------------------------------------------------------
 // a7: forward recursion. The argmax over j of phi_{t-1}(j) + log p(x_i | x^j)
-// is screened in FP32 with a rigorous rounding bound (centred, Q^-1/2-scaled
-// coordinates), and every j that can still be the FP64 maximum is evaluated
-// in FP64; phi_t is accumulated in FP64. Lowest j wins ties.
+// is screened in FP32 with a rigorous rounding bound (centred coordinates
+// scaled by Q^-1/2 kKm, where m~ = kKm^2 |x_i - f_j|^2_{Q^-1}), and every j
+// that can still be the FP64 maximum is evaluated in FP64; phi_t is
+// accumulated in FP64. Lowest j wins ties.
 // On return: best[p], phinew[p] for the block's particles.
 // ---------------------------------------------------------------------------
 template <class M, int PPT>
@@ -507,56 +719,57 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
     for (int j = tid; j < Np; j += NT) {
         const double dphi = s.phis[j] - pmax;
         const float ph = (float)dphi;
+        float fr[D];
+        load_row<D, DP>(s.fs, j, fr);
         float F = 0.0f;
 #pragma unroll
-        for (int c = 0; c < D; ++c) F = fmaf(s.fs[j * DP + c], s.fs[j * DP + c], F);
-        const float B = Ku * (F + fabsf(ph)) +
+        for (int c = 0; c < D; ++c) F = fmaf(fr[c], fr[c], F);
+        const float B = Ku * (kLam * F + fabsf(ph)) +
                         (float)(4.4408920985006262e-16 * (fabs(s.phis[j]) + fabs(pmax)));
         ab[j] = make_float2(ph + B, ph - B);
     }
     __syncthreads();
     float xc[PPT][D], C[PPT], Lmax[PPT];
-    float sq[D], cf[D];
+    float cf[D], qk[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) { sq[c] = mp.sqrt_qinv_f[c]; cf[c] = s.misc[c]; }
+    for (int c = 0; c < D; ++c) {
+        cf[c] = s.misc[c];
+        qk[c] = mp.sqrt_qinv_f[c] * kKm;
+    }
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         const int i = min(tid + p * NT, N - 1);
+        float xr[D];
+        load_row<D, DP>(s.xs, i, xr);
         float X = 0.0f;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            xc[p][c] = (s.xs[i * DP + c] - cf[c]) * sq[c];
+            xc[p][c] = (xr[c] - cf[c]) * qk[c];
             X = fmaf(xc[p][c], xc[p][c], X);
         }
-        C[p] = Ku * X;
+        C[p] = Ku * kLam * X;
         Lmax[p] = -INFINITY;
     }
+    const float cl = -(0.5f + Ku) * kLam, cu = -(0.5f - Ku) * kLam;
     // pass 1: the best guaranteed lower bound
     for (int j = 0; j < Np; ++j) {
         float fj[D];
         load_row<D, DP>(s.fs, j, fj);
         const float am = ab[j].y;
 #pragma unroll
-        for (int p = 0; p < PPT; ++p) {
-            float m = 0.0f;
-#pragma unroll
-            for (int c = 0; c < D; ++c) {
-                const float e = xc[p][c] - fj[c];
-                m = fmaf(e, e, m);
-            }
-            Lmax[p] = fmaxf(Lmax[p], fmaf(-(0.5f + Ku), m, am - C[p]));
-        }
+        for (int p = 0; p < PPT; ++p)
+            Lmax[p] = fmaxf(Lmax[p], fmaf(cl, sqdist<D>(xc[p], fj), am - C[p]));
     }
     // pass 2: FP64 evaluation of every candidate whose upper bound reaches Lmax
-    double bs[PPT], blt[PPT], xd[PPT][D];
+    // (the FP32 particle is re-read from shared memory: candidates are rare)
+    double bs[PPT], blt[PPT];
+    int row[PPT];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
-        const int i = min(tid + p * NT, N - 1);
+        row[p] = min(tid + p * NT, N - 1) * DP;
         bs[p] = -INFINITY;
         blt[p] = 0.0;
         best[p] = 0;
-#pragma unroll
-        for (int c = 0; c < D; ++c) xd[p][c] = (double)s.xs[i * DP + c];
     }
     for (int j = 0; j < Np; ++j) {
         float fj[D];
@@ -564,21 +777,9 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
         const float ap = ab[j].x;
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
-            float m = 0.0f;
-#pragma unroll
-            for (int c = 0; c < D; ++c) {
-                const float e = xc[p][c] - fj[c];
-                m = fmaf(e, e, m);
-            }
-            const float U = fmaf(-(0.5f - Ku), m, ap + C[p]);
+            const float U = fmaf(cu, sqdist<D>(xc[p], fj), ap + C[p]);
             if (U >= Lmax[p]) {
-                double m64 = 0.0;
-#pragma unroll
-                for (int c = 0; c < D; ++c) {
-                    const double e = xd[p][c] - f64[(size_t)j * D + c];
-                    m64 += e * e * mp.qinv[c];
-                }
-                const double lt = mp.logtrans_c - 0.5 * m64;
+                const double lt = mp.logtrans_c - 0.5 * trans_m64<D>(mp, s.xs + row[p], f64 + (size_t)j * D);
                 const double sv = s.phis[j] + lt;
                 if (sv > bs[p]) { bs[p] = sv; blt[p] = lt; best[p] = j; }
             }
@@ -589,13 +790,7 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
         if (bs[p] == -INFINITY) {
             // no candidate passed the screen (non-finite inputs): plain FP64 scan
             for (int j = 0; j < Np; ++j) {
-                double m64 = 0.0;
-#pragma unroll
-                for (int c = 0; c < D; ++c) {
-                    const double e = xd[p][c] - f64[(size_t)j * D + c];
-                    m64 += e * e * mp.qinv[c];
-                }
-                const double lt = mp.logtrans_c - 0.5 * m64;
+                const double lt = mp.logtrans_c - 0.5 * trans_m64<D>(mp, s.xs + row[p], f64 + (size_t)j * D);
                 const double sv = s.phis[j] + lt;
                 if (sv > bs[p]) { bs[p] = sv; blt[p] = lt; best[p] = j; }
             }
@@ -605,8 +800,18 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
     for (int p = 0; p < PPT; ++p) {
         const int i = tid + p * NT;
         if (i >= N) { phinew[p] = 0.0; continue; }
-        phinew[p] = M::loglik64(mp, s.zs, xd[p]) + blt[p] + s.phis[best[p]];
+        double xd[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) xd[c] = (double)s.xs[row[p] + c];
+        phinew[p] = M::loglik64(mp, s.zs, xd) + blt[p] + s.phis[best[p]];
     }
+}
+
+// Extra squared-distance spread the initial noise adds: 2 sum_d q_d.
+__device__ inline float init_spread(const ModelParams& mp) {
+    float v = 0.0f;
+    for (int c = 0; c < mp.d; ++c) v += (float)mp.q[c];
+    return 2.0f * v;
 }
 
 // ---------------------------------------------------------------------------
@@ -621,6 +826,7 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
     const int tid = threadIdx.x, NT = blockDim.x;
     __shared__ int s_item;
     double* f64 = a.f64 + (size_t)blockIdx.x * a.Nmax * D;
+    const float q_extra = init_spread(mp);
     for (;;) {
         __syncthreads();
         if (tid == 0) s_item = atomicAdd(a.queue, 1);
@@ -646,8 +852,12 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
             for (int e = tid; e < N * D; e += NT) s.xs[(e / D) * DP + (e % D)] = src[e];
             for (int j = tid; j < N; j += NT) s.phis[j] = a.phi[(size_t)b * a.Nmax + j];
         }
-        float guess = a.bwguess[b], w = 0.25f;
-        bool have_guess = (t0 > 0) && guess > 0.0f;
+        MedState st;
+        st.med = a.bwguess[b];
+        st.have = (t0 > 0) && st.med > 0.0f;
+        st.trend = 1.0f;
+        st.w = 0.004f;
+        st.fresh = 1;
         int tdone = t0;
         __syncthreads();
         for (int t = t0 + 1; t <= t1; ++t) {
@@ -658,9 +868,11 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
                                    : nullptr;
             prepare_step<M, PPT>(mp, s, t, N, Np, t == 1, a.x0 + (size_t)b * D, yt, f64, a.prior,
                                  a.seed, (uint32_t)b, xin);
-            if (!a.viterbi_only)
-                svgd_iterations<M, PPT>(mp, s, N, Np, a.L, a.eps, a.bw_rule, a.bw_value, a.prior,
-                                        guess, w, have_guess, nullptr, a.status + a.B);
+            if (!a.viterbi_only) {
+                st.fresh = 1;
+                svgd_iterations<M, PPT>(mp, s, N, Np, a.L, a.eps, a.bw_rule, a.bw_value, a.prior, st,
+                                        q_extra, nullptr, a.status + a.B);
+            }
             int best[PPT];
             double phinew[PPT];
             viterbi_step<M, PPT>(mp, s, N, Np, f64, best, phinew);
@@ -696,7 +908,7 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
         for (int j = tid; j < N; j += NT) a.phi[(size_t)b * a.Nmax + j] = s.phis[j];
         if (tid == 0) {
             a.tcur[b] = tdone;
-            a.bwguess[b] = guess;
+            a.bwguess[b] = st.have ? st.med : 0.0f;
         }
     }
 }
@@ -717,10 +929,14 @@ __global__ void __launch_bounds__(MAXT, MINB) debug_svgd_kernel(const __grid_con
     prepare_step<M, PPT>(a.mp, s, a.t, a.N, a.Np, first, a.x0 + (size_t)b * D, a.y + (size_t)b * a.mp.dy,
                          a.f64 + (size_t)b * a.Np * D, a.prior, 0, 0,
                          a.xinit + (size_t)b * a.N * D);
-    float guess = 0.0f, w = 0.25f;
-    bool have_guess = false;
-    svgd_iterations<M, PPT>(a.mp, s, a.N, a.Np, a.iters, a.eps, a.bw_rule, a.bw_value, a.prior, guess,
-                            w, have_guess, a.hout ? a.hout + (size_t)b * a.iters : nullptr, nullptr);
+    MedState st;
+    st.med = 0.0f;
+    st.have = 0;
+    st.trend = 1.0f;
+    st.w = 0.004f;
+    st.fresh = 1;
+    svgd_iterations<M, PPT>(a.mp, s, a.N, a.Np, a.iters, a.eps, a.bw_rule, a.bw_value, a.prior, st,
+                            init_spread(a.mp), a.hout ? a.hout + (size_t)b * a.iters : nullptr, nullptr);
     for (int e = tid; e < a.N * D; e += NT)
         a.xout[(size_t)b * a.N * D + e] = s.xs[(e / D) * DP + (e % D)];
 }

@@ -55,7 +55,7 @@ Carved carve(unsigned char* base, int B, int N, int T, int d, int grid) {
     c.tcur = (int*)take(sizeof(int) * (size_t)B);
     c.Nseq = (int*)take(sizeof(int) * (size_t)B);
     c.Tend = (int*)take(sizeof(int) * (size_t)B);
-    c.status = (int*)take(sizeof(int) * ((size_t)B + 2));
+    c.status = (int*)take(sizeof(int) * ((size_t)B + kStatusExtra));
     c.queue = (int*)take(sizeof(int) * 4);
     c.bwguess = (float*)take(sizeof(float) * (size_t)B);
     c.idx = (int*)take(sizeof(int) * (size_t)B * T);
@@ -66,7 +66,7 @@ Carved carve(unsigned char* base, int B, int N, int T, int d, int grid) {
 // Clears what the previous call left in the shared array.
 __global__ void noalloc_init_kernel(int B, int N, int T, int* tcur, int* Nseq, int* Tend, int* status,
                                     int* queue, float* bwguess) {
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B + 2; b += gridDim.x * blockDim.x) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B + kStatusExtra; b += gridDim.x * blockDim.x) {
         status[b] = 0;
         if (b < B) {
             tcur[b] = 0;
@@ -140,7 +140,7 @@ extern "C" smap_status smap_viterbi_noalloc(int model, const double* params, int
     }
 
     cudaStream_t st = (cudaStream_t)stream;
-    noalloc_init_kernel<<<(B + 2 + 255) / 256, 256, 0, st>>>(B, N, T, c.tcur, c.Nseq, c.Tend, c.status,
+    noalloc_init_kernel<<<(B + kStatusExtra + 255) / 256, 256, 0, st>>>(B, N, T, c.tcur, c.Nseq, c.Tend, c.status,
                                                              c.queue, c.bwguess);
     SeqArgs a;
     memset(&a, 0, sizeof(a));

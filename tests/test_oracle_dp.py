@@ -127,3 +127,27 @@ def test_map_path_tends_to_rts_smoother(oracle):
         gaps.append(np.mean(g))
     assert gaps[0] > gaps[1] > gaps[2]
     assert gaps[2] < 0.7 * gaps[0]
+
+
+def test_margins_against_direct_scipy(oracle):
+    """The margin helper used by the GPU tests: best minus second best of
+    phi_{t-1}(j) + log N(x_t^i; f(x_{t-1}^j), Q), computed here with scipy."""
+    wl = W.make_linear_gauss(B=1, T=4, N=5)
+    rng = np.random.default_rng(2)
+    hist = wl.truth[0, 1:, None, :] + 0.3 * rng.normal(0, 1, (4, 5, 4))
+    z = wl.y[0].astype(np.float64)
+    F = np.block([[np.eye(2), 0.1 * np.eye(2)], [np.zeros((2, 2)), np.eye(2)]])
+    Q = 0.01 * np.eye(4)
+    got = oracle.viterbi_margins(wl.kind, wl.params, wl.x0[0], hist, z)
+    assert np.all(np.isinf(got[0]))
+    phi = np.array([stats.multivariate_normal.logpdf(z[0], hist[0, i, :2], 0.05 * np.eye(2))
+                    + stats.multivariate_normal.logpdf(hist[0, i], F @ wl.x0[0], Q) for i in range(5)])
+    for t in range(1, 4):
+        S = np.array([[stats.multivariate_normal.logpdf(hist[t, i], F @ hist[t - 1, j], Q) + phi[j]
+                       for j in range(5)] for i in range(5)])
+        srt = np.sort(S, axis=1)
+        expect = (srt[:, -1] - srt[:, -2]) / np.maximum(1.0, np.abs(srt[:, -1]))
+        assert np.allclose(got[t], expect, rtol=1e-9, atol=1e-12)
+        best = S.max(1)
+        phi = best + np.array([stats.multivariate_normal.logpdf(z[t], hist[t, i, :2], 0.05 * np.eye(2))
+                               for i in range(5)])
