@@ -41,6 +41,16 @@ def shard(rank: int, world: int, B: int):
     return list(range(rank * B, (rank + 1) * B))
 
 
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The slowest rank's time (the job's time under weak scaling)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_workload(rank: int, B: int, T: int, N: int, L: int):
     wl = W.make_range_cv(B=B, T=T, N=N, L=L, seed=2 + rank, first=rank * B)
     return wl
@@ -236,11 +246,8 @@ def main():
     torch.cuda.synchronize()
     launches = abi.smap_kernel_launches() - launches0
     clk = clocks.stop()
-    ms = float(np.mean(step_ms))
+    ms = max_over_ranks(float(np.mean(step_ms)), dist, f"cuda:{local}")
     if dist:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     units_rank = wl.particle_updates()
     value = units_rank * world / (ms / 1000.0)
@@ -256,11 +263,7 @@ def main():
         abi.smap_run_batch(est.h, y_pin, None, None, path_pin, J_pin)
         if k:
             e2e_t.append(time.perf_counter() - t0)
-    e2e_s = float(np.mean(e2e_t))
-    if dist:
-        t = torch.tensor([e2e_s], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(float(np.mean(e2e_t)), dist, f"cuda:{local}")
 
     if rank != 0:
         est.close()

@@ -68,7 +68,10 @@ def test_full_size_config(oracle, torch, name):
         assert np.array_equal(psi[k, :T][ok], ref["psi"][ok]), f"seq {b}: backpointers differ"
         assert J[b] == pytest.approx(ref["J"], rel=1e-12), f"seq {b}: J differs"
         assert np.array_equal(path[b, : T + 1], ref["path"].astype(np.float32)), f"seq {b}: path differs"
-        assert m.path_score(path[b, : T + 1].astype(np.float64), z) == pytest.approx(J[b], rel=1e-9)
+        # row 0 of the FP32 path is x_0 rounded; the recursion uses x_0 in FP64
+        p64 = path[b, : T + 1].astype(np.float64)
+        p64[0] = wl.x0[b]
+        assert m.path_score(p64, z) == pytest.approx(J[b], rel=1e-12)
         # one SVGD step from the GPU's previous set, re-run in FP64
         for t in sorted(set([2] + list(rng.integers(3, T + 1, svgd_steps - 1)))):
             xprev = Hb[t - 2]
