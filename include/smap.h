@@ -192,6 +192,67 @@ smap_status smap_viterbi_noalloc(int model, const double* params, int n_params, 
                                  const double* x0, const float* hist, const float* y, float* path,
                                  double* J, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned proposal. (Not in the paper: a transport map that replaces most of
+ * the SVGD iterations of a step.) A 3-layer perceptron, features -> 256 ->
+ * 256 -> d with GELU, BF16 weights and activations on the tensor cores, FP32
+ * accumulation, maps a propagated particle u = f_t(x_{t-1}^i) + Q^{1/2} xi
+ * (the plain initialisation) and the observation z_t to the displacement that
+ * plain SVGD applies to it; the learned step then starts from u + MLP(u, z_t)
+ * and runs a few SVGD iterations. Features (at most 32 per row, zero padded):
+ *   PLANAR_ARM   [u, z, z - h(u)]
+ *   CLUTTER_CV2D [velocity, the M points relative to the position, nearest first]
+ *   others       [u, z (unheard = 0), heard flags]
+ * Training data rows are [32] FP32 features and [16] FP32 displacement targets
+ * (zero padded). Parameters: FP32 master vector, padded layout W1 [256][32],
+ * b1 [256], W2 [256][256], b2 [256], W3 [16][256], b3 [16]; normalisation
+ * vector mu_in [32], sd_in [32], mu_out [16], sd_out [16] (inputs and targets
+ * are standardised with them). The loss is the mean squared error of the
+ * standardised displacement over the d real outputs; the update is Adam
+ * (Kingma & Ba 2015) with a cosine learning-rate decay.
+ * All pointers of these calls are device pointers unless stated.
+ * ------------------------------------------------------------------------- */
+typedef struct smap_proposal smap_proposal;
+
+/* Creates a proposal for a model (parameters as in smap_config, host memory),
+ * weights uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) from `seed`. */
+smap_status smap_proposal_create(int model, const double* params, int n_params, uint64_t seed, void* stream,
+                                 smap_proposal** out);
+void smap_proposal_destroy(smap_proposal* p);
+smap_status smap_proposal_dims(const smap_proposal* p, int* in, int* out, int* hidden, long* n_params);
+/* Host copies of the FP32 parameters / normalisation (either may be NULL). */
+smap_status smap_proposal_get_weights(smap_proposal* p, float* theta, float* norm);
+smap_status smap_proposal_set_weights(smap_proposal* p, const float* theta, const float* norm);
+/* Normalisation from data: column means and standard deviations. */
+smap_status smap_proposal_fit_normalization(smap_proposal* p, const float* feat, const float* targ, long rows);
+/* disp [rows][d] = displacement predicted for feat [rows][32]. Synchronous. */
+smap_status smap_proposal_forward(smap_proposal* p, const float* feat, long rows, float* disp);
+/* One forward and backward pass over all `rows` (no update): gradient of the
+ * loss w.r.t. the parameters (host [n_params], may be NULL) and the loss
+ * (host, may be NULL). */
+smap_status smap_proposal_loss_grad(smap_proposal* p, const float* feat, const float* targ, long rows,
+                                    float* grad, double* loss);
+/* `steps` Adam steps on minibatches of `batch` rows drawn (Philox) from the
+ * n_rows training rows; learning rate decays from lr to lr_final; loss_curve
+ * (host [steps], may be NULL) receives each minibatch loss. */
+smap_status smap_proposal_train(smap_proposal* p, const float* feat, const float* targ, long n_rows, int steps,
+                                int batch, double lr, double lr_final, float* loss_curve);
+const char* smap_proposal_last_error(const smap_proposal* p);
+
+/* Training rows from the handle's last run (smap_run_batch with no proposal
+ * attached): for every sequence b, step t <= T_b and particle i < N_b, the
+ * features of the plain initialisation u and the target x_t^i - u. Rows are
+ * ordered by (b, t, i). feat [max_rows][32], targ [max_rows][16] (device);
+ * *rows receives the number written; SMAP_E_INVAL if max_rows is too small. */
+smap_status smap_proposal_capture(smap_proposal* p, smap_handle* h, float* feat, float* targ, long max_rows,
+                                  long* rows);
+
+/* Attaches a proposal to a handle (p = NULL detaches): smap_run_batch then
+ * initialises each step from u + MLP(u, z_t) and runs L_learned SVGD
+ * iterations, one graph-captured launch sequence per time step. The proposal
+ * must outlive the attachment. */
+smap_status smap_set_proposal(smap_handle* h, smap_proposal* p, int L_learned);
+
 /* Kernel variant (particles per thread, block size) used by the step kernels.
  * smap_autotune times every compiled variant on the first min(B, sample)
  * sequences for `steps` steps of y_all (layout as in smap_run_batch, host or

@@ -99,6 +99,14 @@ def lib():
                                           _D, _D, _D, _I, _D, _D, _D]
             L.om_viterbi_margins.argtypes = [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              _D, _D, _D, _D]
+            L.om_mlp_nparams.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            L.om_mlp_nparams.restype = ctypes.c_long
+            L.om_mlp_forward.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, ctypes.c_long, _D, _D]
+            L.om_mlp_loss_grad.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, ctypes.c_long, _D, _D, _D]
+            L.om_mlp_loss_grad.restype = ctypes.c_double
+            L.om_adam.argtypes = [ctypes.c_long, _D, _D, _D, _D, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double]
+            L.om_proposal_features.argtypes = [ctypes.c_int, _D, ctypes.c_int, _D, _D, _D]
             L.om_run_batch.argtypes = [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                        ctypes.c_uint64, ctypes.c_int, _I, _D, ctypes.c_int, _I, _D,
@@ -268,6 +276,42 @@ def viterbi_margins(kind, params, x0, hist, z):
     if rc != 0:
         raise ValueError("oracle: viterbi_margins rejected its input")
     return out
+
+
+def mlp_nparams(n_in, H, n_out):
+    return int(lib().om_mlp_nparams(n_in, H, n_out))
+
+
+def mlp_forward(n_in, H, n_out, W, X):
+    """3-layer GELU perceptron, packed W = [W1, b1, W2, b2, W3, b3]."""
+    W = _f64(W); X = _f64(X).reshape(-1, n_in)
+    Y = np.empty((X.shape[0], n_out))
+    lib().om_mlp_forward(n_in, H, n_out, _dp(W), X.shape[0], _dp(X), _dp(Y))
+    return Y
+
+
+def mlp_loss_grad(n_in, H, n_out, W, X, Tg):
+    """(loss, gradient): mean squared error over rows and outputs."""
+    W = _f64(W); X = _f64(X).reshape(-1, n_in); Tg = _f64(Tg).reshape(-1, n_out)
+    G = np.empty_like(W)
+    loss = lib().om_mlp_loss_grad(n_in, H, n_out, _dp(W), X.shape[0], _dp(X), _dp(Tg), _dp(G))
+    return loss, G
+
+
+def adam(theta, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step in place on float64 arrays."""
+    for a in (theta, g, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    lib().om_adam(len(theta), _dp(theta), _dp(g), _dp(m), _dp(v), int(t), float(lr), beta1, beta2, eps)
+
+
+def proposal_features(kind, params, u, z):
+    params = _f64(params); u = _f64(u); z = _f64(z)
+    f = np.zeros(32)
+    n = lib().om_proposal_features(int(kind), _dp(params), len(params), _dp(u), _dp(z), _dp(f))
+    if n < 0:
+        raise ValueError("oracle: bad model")
+    return f[:n]
 
 
 def run_batch(kind, params, N, L, eps, bw_rule, bw_value, prior, seed, seq_ids, x0, z, T,

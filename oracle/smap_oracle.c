@@ -709,3 +709,181 @@ int om_run_batch(int kind, const double* params, int np, int N, int L, double ep
     }
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned proposal: a 3-layer perceptron in -> H -> H -> out, GELU after    */
+/* the two hidden layers, trained by mean squared error with Adam. This part */
+/* is not in the paper (the build adds it); the oracle is the plain FP64     */
+/* definition used to check the GPU's forward and backward passes.           */
+/* Packed parameters: W1 [H][in], b1 [H], W2 [H][H], b2 [H], W3 [out][H],    */
+/* b3 [out]. GELU in its tanh form (Hendrycks & Gimpel 2016):                */
+/*   gelu(x) = x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))).                */
+/* ------------------------------------------------------------------------ */
+static double om_gelu(double x)
+{
+    const double k0 = 0.7978845608028654, k1 = 0.044715;
+    return 0.5 * x * (1.0 + tanh(k0 * (x + k1 * x * x * x)));
+}
+
+static double om_gelu_grad(double x)
+{
+    const double k0 = 0.7978845608028654, k1 = 0.044715;
+    double u = k0 * (x + k1 * x * x * x), th = tanh(u);
+    return 0.5 * (1.0 + th) + 0.5 * x * (1.0 - th * th) * k0 * (1.0 + 3.0 * k1 * x * x);
+}
+
+long om_mlp_nparams(int in, int H, int out)
+{
+    return (long)H * in + H + (long)H * H + H + (long)out * H + out;
+}
+
+/* y = MLP(x) for `rows` rows of X [rows][in]; Y [rows][out]. */
+void om_mlp_forward(int in, int H, int out, const double* W, long rows, const double* X, double* Y)
+{
+    const double *W1 = W, *b1 = W1 + (long)H * in, *W2 = b1 + H, *b2 = W2 + (long)H * H;
+    const double *W3 = b2 + H, *b3 = W3 + (long)out * H;
+    double* h1 = (double*)malloc(sizeof(double) * H);
+    double* h2 = (double*)malloc(sizeof(double) * H);
+    for (long r = 0; r < rows; ++r) {
+        const double* x = X + r * in;
+        for (int j = 0; j < H; ++j) {
+            double z = b1[j];
+            for (int k = 0; k < in; ++k) z += W1[(long)j * in + k] * x[k];
+            h1[j] = om_gelu(z);
+        }
+        for (int j = 0; j < H; ++j) {
+            double z = b2[j];
+            for (int k = 0; k < H; ++k) z += W2[(long)j * H + k] * h1[k];
+            h2[j] = om_gelu(z);
+        }
+        for (int o = 0; o < out; ++o) {
+            double z = b3[o];
+            for (int k = 0; k < H; ++k) z += W3[(long)o * H + k] * h2[k];
+            Y[r * out + o] = z;
+        }
+    }
+    free(h1); free(h2);
+}
+
+/* loss = mean over rows and outputs of (y - t)^2 and its gradient G (packed
+ * like W) by the chain rule, row by row. Returns the loss. */
+double om_mlp_loss_grad(int in, int H, int out, const double* W, long rows, const double* X,
+                        const double* Tg, double* G)
+{
+    const double *W1 = W, *b1 = W1 + (long)H * in, *W2 = b1 + H, *b2 = W2 + (long)H * H;
+    const double *W3 = b2 + H, *b3 = W3 + (long)out * H;
+    double *G1 = G, *g1 = G1 + (long)H * in, *G2 = g1 + H, *g2 = G2 + (long)H * H;
+    double *G3 = g2 + H, *g3 = G3 + (long)out * H;
+    long np = om_mlp_nparams(in, H, out);
+    for (long k = 0; k < np; ++k) G[k] = 0.0;
+    double* z1 = (double*)malloc(sizeof(double) * H);
+    double* h1 = (double*)malloc(sizeof(double) * H);
+    double* z2 = (double*)malloc(sizeof(double) * H);
+    double* h2 = (double*)malloc(sizeof(double) * H);
+    double* dy = (double*)malloc(sizeof(double) * out);
+    double* d2 = (double*)malloc(sizeof(double) * H);
+    double* d1 = (double*)malloc(sizeof(double) * H);
+    double loss = 0.0, scale = 1.0 / ((double)rows * out);
+    for (long r = 0; r < rows; ++r) {
+        const double* x = X + r * in;
+        for (int j = 0; j < H; ++j) {
+            double z = b1[j];
+            for (int k = 0; k < in; ++k) z += W1[(long)j * in + k] * x[k];
+            z1[j] = z; h1[j] = om_gelu(z);
+        }
+        for (int j = 0; j < H; ++j) {
+            double z = b2[j];
+            for (int k = 0; k < H; ++k) z += W2[(long)j * H + k] * h1[k];
+            z2[j] = z; h2[j] = om_gelu(z);
+        }
+        for (int o = 0; o < out; ++o) {
+            double z = b3[o];
+            for (int k = 0; k < H; ++k) z += W3[(long)o * H + k] * h2[k];
+            double e = z - Tg[r * out + o];
+            loss += e * e * scale;
+            dy[o] = 2.0 * e * scale;
+        }
+        /* layer 3 */
+        for (int o = 0; o < out; ++o) {
+            g3[o] += dy[o];
+            for (int k = 0; k < H; ++k) G3[(long)o * H + k] += dy[o] * h2[k];
+        }
+        for (int k = 0; k < H; ++k) {
+            double s = 0.0;
+            for (int o = 0; o < out; ++o) s += dy[o] * W3[(long)o * H + k];
+            d2[k] = s * om_gelu_grad(z2[k]);
+        }
+        /* layer 2 */
+        for (int j = 0; j < H; ++j) {
+            g2[j] += d2[j];
+            for (int k = 0; k < H; ++k) G2[(long)j * H + k] += d2[j] * h1[k];
+        }
+        for (int k = 0; k < H; ++k) {
+            double s = 0.0;
+            for (int j = 0; j < H; ++j) s += d2[j] * W2[(long)j * H + k];
+            d1[k] = s * om_gelu_grad(z1[k]);
+        }
+        /* layer 1 */
+        for (int j = 0; j < H; ++j) {
+            g1[j] += d1[j];
+            for (int k = 0; k < in; ++k) G1[(long)j * in + k] += d1[j] * x[k];
+        }
+    }
+    free(z1); free(h1); free(z2); free(h2); free(dy); free(d2); free(d1);
+    return loss;
+}
+
+/* One Adam step (Kingma & Ba 2015) with bias correction, step count t >= 1. */
+void om_adam(long n, double* theta, const double* g, double* m, double* v, int t, double lr,
+             double beta1, double beta2, double eps)
+{
+    double c1 = 1.0 - pow(beta1, t), c2 = 1.0 - pow(beta2, t);
+    for (long k = 0; k < n; ++k) {
+        m[k] = beta1 * m[k] + (1.0 - beta1) * g[k];
+        v[k] = beta2 * v[k] + (1.0 - beta2) * g[k] * g[k];
+        theta[k] -= lr * (m[k] / c1) / (sqrt(v[k] / c2) + eps);
+    }
+}
+
+/* Proposal features of a propagated particle u and observation z (at most 32):
+ *   PLANAR_ARM   [u, z, z - h(u)]
+ *   CLUTTER_CV2D [velocity, z_m - position for the points nearest first]
+ *   others       [u, z with NaN -> 0, 1 where z is a number]
+ * Returns the count. */
+int om_proposal_features(int kind, const double* params, int np, const double* u, const double* z,
+                         double* f)
+{
+    om_model m;
+    if (om_setup(&m, kind, params, np)) return -1;
+    int d = m.d, n = 0;
+    if (kind == OM_PLANAR_ARM) {
+        double e[2];
+        om_arm_fk(&m, u, e, NULL);
+        for (int c = 0; c < d; ++c) f[n++] = u[c];
+        f[n++] = z[0]; f[n++] = z[1];
+        f[n++] = z[0] - e[0]; f[n++] = z[1] - e[1];
+    } else if (kind == OM_CLUTTER_CV2D) {
+        int M = (int)m.p[6], nm = M < 15 ? M : 15;
+        double dist[32];
+        int used[32] = {0};
+        f[n++] = u[2]; f[n++] = u[3];
+        for (int k = 0; k < M; ++k) {
+            double ex = z[2 * k] - u[0], ey = z[2 * k + 1] - u[1];
+            dist[k] = ex * ex + ey * ey;
+        }
+        for (int r = 0; r < nm; ++r) {          /* nearest remaining point */
+            int best = -1;
+            for (int k = 0; k < M; ++k)
+                if (!used[k] && (best < 0 || dist[k] < dist[best])) best = k;
+            used[best] = 1;
+            f[n++] = z[2 * best] - u[0];
+            f[n++] = z[2 * best + 1] - u[1];
+        }
+    } else {
+        int dy = m.dy < (32 - d) / 2 ? m.dy : (32 - d) / 2;
+        for (int c = 0; c < d; ++c) f[n++] = u[c];
+        for (int c = 0; c < dy; ++c) f[n++] = isnan(z[c]) ? 0.0 : z[c];
+        for (int c = 0; c < dy; ++c) f[n++] = isnan(z[c]) ? 0.0 : 1.0;
+    }
+    return n;
+}

@@ -31,7 +31,12 @@ EXPORTS = [
     "smap_get_variant", "smap_debug_svgd", "smap_debug_philox", "smap_debug_normals",
     "smap_kernel_launches", "smap_status_string", "smap_last_error", "smap_last_kernel_ms",
     "smap_viterbi_noalloc", "smap_debug_median_stats",
+    "smap_proposal_create", "smap_proposal_destroy", "smap_proposal_dims", "smap_proposal_get_weights",
+    "smap_proposal_set_weights", "smap_proposal_fit_normalization", "smap_proposal_forward",
+    "smap_proposal_loss_grad", "smap_proposal_train", "smap_proposal_last_error", "smap_proposal_capture",
+    "smap_set_proposal",
 ]
+MLP_IN_P, MLP_OUT_P, MLP_H = 32, 16, 256
 
 
 class SmapError(RuntimeError):
@@ -91,6 +96,23 @@ def load():
     L.smap_debug_normals.argtypes = [ctypes.c_uint64, u32, u32, u32, _I, _I, _VP]
     L.smap_last_kernel_ms.argtypes = [_VP, _VP, _VP]
     L.smap_debug_median_stats.argtypes = [_VP, _VP]
+    L.smap_proposal_create.argtypes = [_I, ctypes.POINTER(ctypes.c_double), _I, ctypes.c_uint64, _VP,
+                                       ctypes.POINTER(_VP)]
+    L.smap_proposal_destroy.argtypes = [_VP]
+    L.smap_proposal_destroy.restype = None
+    L.smap_proposal_dims.argtypes = [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                     ctypes.POINTER(ctypes.c_long)]
+    L.smap_proposal_get_weights.argtypes = [_VP, _VP, _VP]
+    L.smap_proposal_set_weights.argtypes = [_VP, _VP, _VP]
+    L.smap_proposal_fit_normalization.argtypes = [_VP, _VP, _VP, ctypes.c_long]
+    L.smap_proposal_forward.argtypes = [_VP, _VP, ctypes.c_long, _VP]
+    L.smap_proposal_loss_grad.argtypes = [_VP, _VP, _VP, ctypes.c_long, _VP, _VP]
+    L.smap_proposal_train.argtypes = [_VP, _VP, _VP, ctypes.c_long, _I, _I, ctypes.c_double, ctypes.c_double,
+                                      _VP]
+    L.smap_proposal_last_error.argtypes = [_VP]
+    L.smap_proposal_last_error.restype = ctypes.c_char_p
+    L.smap_proposal_capture.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_long, ctypes.POINTER(ctypes.c_long)]
+    L.smap_set_proposal.argtypes = [_VP, _VP, _I]
     L.smap_viterbi_noalloc.argtypes = [_I, ctypes.POINTER(ctypes.c_double), _I, _I, _I, _I,
                                        _VP, _VP, _VP, _VP, _VP, _VP]
     L.smap_kernel_launches.argtypes = []
@@ -325,6 +347,96 @@ def smap_debug_median_stats(h):
     out = np.zeros(3, np.int32)
     _check(load().smap_debug_median_stats(h, ctypes.c_void_p(out.ctypes.data)), h)
     return tuple(int(v) for v in out)
+
+
+# ------------------------------------------------------------- proposal ----
+def _pcheck(st, p):
+    if st != SMAP_OK:
+        L = load()
+        raise SmapError(st, L.smap_proposal_last_error(p).decode() or L.smap_status_string(st).decode())
+
+
+def _dev(a, dtype):
+    p, dev, _ = _arg(a, dtype, True)
+    if dev != 1:
+        raise ValueError("this call takes CUDA tensors")
+    return p
+
+
+def smap_proposal_create(model, params, seed=1, stream=None):
+    params = np.ascontiguousarray(params, dtype=np.float64).ravel()
+    p = ctypes.c_void_p()
+    st = load().smap_proposal_create(int(model), params.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     len(params), ctypes.c_uint64(int(seed)), _stream_ptr(stream), ctypes.byref(p))
+    if st != SMAP_OK:
+        raise SmapError(st, load().smap_status_string(st).decode())
+    return p
+
+
+def smap_proposal_destroy(p):
+    load().smap_proposal_destroy(p)
+
+
+def smap_proposal_dims(p):
+    a, b, c, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_long()
+    _pcheck(load().smap_proposal_dims(p, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(n)), p)
+    return a.value, b.value, c.value, n.value
+
+
+def smap_proposal_get_weights(p):
+    n = smap_proposal_dims(p)[3]
+    theta = np.empty(n, np.float32)
+    norm = np.empty(2 * MLP_IN_P + 2 * MLP_OUT_P, np.float32)
+    _pcheck(load().smap_proposal_get_weights(p, ctypes.c_void_p(theta.ctypes.data), ctypes.c_void_p(norm.ctypes.data)), p)
+    return theta, norm
+
+
+def smap_proposal_set_weights(p, theta=None, norm=None):
+    t = None if theta is None else np.ascontiguousarray(theta, np.float32)
+    n = None if norm is None else np.ascontiguousarray(norm, np.float32)
+    _pcheck(load().smap_proposal_set_weights(p, None if t is None else ctypes.c_void_p(t.ctypes.data),
+                                             None if n is None else ctypes.c_void_p(n.ctypes.data)), p)
+
+
+def smap_proposal_fit_normalization(p, feat, targ):
+    _pcheck(load().smap_proposal_fit_normalization(p, _dev(feat, np.float32), _dev(targ, np.float32),
+                                                   int(feat.shape[0])), p)
+
+
+def smap_proposal_forward(p, feat, disp):
+    _pcheck(load().smap_proposal_forward(p, _dev(feat, np.float32), int(feat.shape[0]), _dev(disp, np.float32)), p)
+
+
+def smap_proposal_loss_grad(p, feat, targ):
+    n = smap_proposal_dims(p)[3]
+    g = np.empty(n, np.float32)
+    loss = ctypes.c_double()
+    _pcheck(load().smap_proposal_loss_grad(p, _dev(feat, np.float32), _dev(targ, np.float32), int(feat.shape[0]),
+                                           ctypes.c_void_p(g.ctypes.data), ctypes.byref(loss)), p)
+    return loss.value, g
+
+
+def smap_proposal_train(p, feat, targ, steps, batch, lr, lr_final):
+    curve = np.empty(max(int(steps), 1), np.float32)
+    _pcheck(load().smap_proposal_train(p, _dev(feat, np.float32), _dev(targ, np.float32), int(feat.shape[0]),
+                                       int(steps), int(batch), float(lr), float(lr_final),
+                                       ctypes.c_void_p(curve.ctypes.data)), p)
+    return curve[: int(steps)]
+
+
+def smap_proposal_last_error(p):
+    return load().smap_proposal_last_error(p).decode()
+
+
+def smap_proposal_capture(p, h, feat, targ):
+    rows = ctypes.c_long()
+    _check(load().smap_proposal_capture(p, h, _dev(feat, np.float32), _dev(targ, np.float32), int(feat.shape[0]),
+                                        ctypes.byref(rows)), h)
+    return rows.value
+
+
+def smap_set_proposal(h, p, L_learned):
+    _check(load().smap_set_proposal(h, p, int(L_learned)), h)
 
 
 def smap_kernel_launches():

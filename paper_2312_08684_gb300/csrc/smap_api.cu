@@ -239,6 +239,12 @@ struct smap_handle {
     uint8_t* active_h = nullptr;
     cudaEvent_t step_done = nullptr;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // batch start, kernel end, batch end
+    // learned proposal (attached with smap_set_proposal) and its step buffers
+    smap_proposal* prop = nullptr;
+    int L_learned = 5;
+    float* lfeat = nullptr;    // [B][Nmax][32]
+    float* lu = nullptr;       // [B][Nmax][d]
+    float* lxinit = nullptr;   // [B][Nmax][d]
 };
 
 namespace {
@@ -280,9 +286,18 @@ smap_status configure_kernel(smap_handle* h, const void* fn, size_t smem) {
     return SMAP_OK;
 }
 
+// Options of a one-step launch (mode 1) beyond the handle's configuration.
+struct StepOpts {
+    const float* xinit = nullptr;   // initial particles of the step [B][Nmax][d]
+    int y_full = 0;                 // y is [B][maxT][dy]
+    int skip_done = 0;              // skip sequences with tcur >= Tend
+    int L = -1;                     // SVGD iterations (-1: the handle's L)
+};
+
 // Launches the sequence kernel of variant v over `items` work items.
 smap_status launch_seq(smap_handle* h, int v, int items, int mode, const float* y, int viterbi_only,
-                       const int* order, int* grid_out = nullptr, int* threads_out = nullptr) {
+                       const int* order, int* grid_out = nullptr, int* threads_out = nullptr,
+                       const StepOpts& opts = StepOpts()) {
     const int nt = variant_threads(v, h->Nmax);
     if (!nt) return fail(h, SMAP_E_UNSUPPORTED, "kernel variant cannot hold N particles");
     const void* fn = h->K->seq[v];
@@ -321,6 +336,10 @@ smap_status launch_seq(smap_handle* h, int v, int items, int mode, const float* 
     a.status = h->status;
     a.queue = h->queue;
     a.viterbi_only = viterbi_only;
+    a.xinit = opts.xinit;
+    a.y_full = opts.y_full;
+    a.skip_done = opts.skip_done;
+    if (opts.L >= 0) a.L = opts.L;
     void* args[] = {&a};
     SMAP_CUDA(h, cudaMemsetAsync(h->queue, 0, sizeof(int), h->stream));
     SMAP_CUDA(h, cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, smem, h->stream));
@@ -411,8 +430,32 @@ smap_status batch_device_work(smap_handle* h, int v) {
     SMAP_CUDA(h, cudaEventRecordWithFlags(h->ev[0], h->stream, cudaEventRecordExternal));
     smap_status st = reset_device_state(h);
     if (st) return st;
-    st = launch_seq(h, v, h->B, 0, h->y, 0, h->order);
-    if (st) return st;
+    if (h->prop) {
+        // learned initialisation: per step, rows (u, features) -> MLP -> one
+        // step of L_learned SVGD iterations for every unfinished sequence
+        ProposalRowsArgs ra;
+        memset(&ra, 0, sizeof(ra));
+        ra.mp = h->mp;
+        ra.B = h->B; ra.Nmax = h->Nmax; ra.maxT = h->maxT; ra.capture = 0;
+        ra.seed = h->cfg.seed;
+        ra.x0 = h->x0; ra.hist = h->hist; ra.y = h->y;
+        ra.tcur = h->tcur; ra.Tend = h->Tend; ra.Nseq = h->Nseq;
+        ra.feat = h->lfeat; ra.u = h->lu;
+        StepOpts so;
+        so.xinit = h->lxinit;
+        so.y_full = 1;
+        so.skip_done = 1;
+        so.L = h->L_learned;
+        for (int t = 1; t <= h->maxT; ++t) {
+            st = proposal_launch_init(h->prop, ra, h->lxinit, h->stream);
+            if (st) return fail(h, st, smap_proposal_last_error(h->prop));
+            st = launch_seq(h, v, h->B, 1, h->y, 0, h->order, nullptr, nullptr, so);
+            if (st) return st;
+        }
+    } else {
+        st = launch_seq(h, v, h->B, 0, h->y, 0, h->order);
+        if (st) return st;
+    }
     SMAP_CUDA(h, cudaEventRecordWithFlags(h->ev[1], h->stream, cudaEventRecordExternal));
     st = launch_backtrack(h);
     if (st) return st;
@@ -441,6 +484,65 @@ const char* smap_status_string(smap_status s) {
 const char* smap_last_error(const smap_handle* h) { return h ? h->err.c_str() : "null handle"; }
 
 uint64_t smap_kernel_launches(void) { return g_launches.load(); }
+
+smap_status smap_set_proposal(smap_handle* h, smap_proposal* p, int L_learned) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    if (p && (proposal_kind(p) != h->mp.kind || proposal_d(p) != h->d))
+        return fail(h, SMAP_E_INVAL, "proposal was made for another model");
+    if (L_learned < 0) return fail(h, SMAP_E_INVAL, "L_learned < 0");
+    if (p && !h->lfeat) {
+        const size_t rows = (size_t)h->B * h->Nmax;
+        if (cudaMalloc(&h->lfeat, sizeof(float) * rows * 32) != cudaSuccess ||
+            cudaMalloc(&h->lu, sizeof(float) * rows * h->d) != cudaSuccess ||
+            cudaMalloc(&h->lxinit, sizeof(float) * rows * h->d) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, SMAP_E_NOMEM, "learned-step buffers");
+        }
+    }
+    h->prop = p;
+    h->L_learned = L_learned;
+    if (h->graph) {   // the device work changes: record a new graph
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    return SMAP_OK;
+}
+
+smap_status smap_proposal_capture(smap_proposal* p, smap_handle* h, float* feat, float* targ, long max_rows,
+                                  long* rows) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    if (!p || !feat || !targ) return fail(h, SMAP_E_INVAL, "null argument");
+    if (proposal_kind(p) != h->mp.kind) return fail(h, SMAP_E_INVAL, "proposal was made for another model");
+    std::vector<long long> base((size_t)h->B * h->maxT, 0);
+    long long total = 0;
+    for (int b = 0; b < h->B; ++b)
+        for (int t = 1; t <= h->tcur_h[b]; ++t) {
+            base[(size_t)b * h->maxT + (t - 1)] = total;
+            total += h->Nseq_h[b];
+        }
+    if (rows) *rows = (long)total;
+    if (total > max_rows) return fail(h, SMAP_E_INVAL, "capture needs " + std::to_string(total) + " rows");
+    long long* dbase = nullptr;
+    SMAP_CUDA(h, cudaMalloc(&dbase, sizeof(long long) * base.size()));
+    cudaError_t e = cudaMemcpyAsync(dbase, base.data(), sizeof(long long) * base.size(), cudaMemcpyHostToDevice,
+                                    h->stream);
+    ProposalRowsArgs ra;
+    memset(&ra, 0, sizeof(ra));
+    ra.mp = h->mp;
+    ra.B = h->B; ra.Nmax = h->Nmax; ra.maxT = h->maxT; ra.capture = 1;
+    ra.seed = h->cfg.seed;
+    ra.x0 = h->x0; ra.hist = h->hist; ra.y = h->y;
+    ra.tcur = h->tcur; ra.Tend = h->tcur; ra.Nseq = h->Nseq;
+    ra.row_base = dbase;
+    ra.feat = feat; ra.targ = targ;
+    if (e == cudaSuccess) st = proposal_launch_capture(p, ra, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dbase);
+    if (e != cudaSuccess) return cuda_fail(h, e, "smap_proposal_capture");
+    return st;
+}
 
 smap_status smap_debug_median_stats(smap_handle* h, int* counts) {
     smap_status st = check_usable(h);
@@ -475,6 +577,8 @@ void smap_destroy(smap_handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->step_done) cudaEventDestroy(h->step_done);
+    for (void* q : {(void*)h->lfeat, (void*)h->lu, (void*)h->lxinit})
+        if (q) cudaFree(q);
     for (cudaEvent_t ev : h->ev)
         if (ev) cudaEventDestroy(ev);
     if (h->ystep_h) cudaFreeHost(h->ystep_h);

@@ -51,6 +51,9 @@ struct SeqArgs {
     int* status;              // [B] per-sequence status (0 or an smap_status)
     int* queue;               // [1] work-queue head
     int viterbi_only;         // 1: particle sets are given in hist (no SVGD)
+    const float* xinit;       // mode 1: [B][Nmax][d] initial particles of the step, or null
+    int y_full;               // mode 1: y is [B][maxT][dy] (indexed by the step)
+    int skip_done;            // mode 1: skip sequences with tcur >= Tend
 };
 
 // Arguments of the debug SVGD kernel.

@@ -4,6 +4,7 @@
 #include <atomic>
 #include <string>
 
+#include "smap.h"
 #include "smap_common.cuh"
 
 namespace smap {
@@ -27,6 +28,33 @@ ModelKernels kernels_range_cv();
 ModelKernels kernels_clutter_cv();
 ModelKernels kernels_planar_arm7();
 ModelKernels kernels_linear_gauss();
+
+// Rows of the learned proposal: propagated particles u = f_t(x_{t-1}^i) + noise
+// (drawn exactly like the step kernels' initialisation) and their features.
+//   capture = 0: one row per (b, i) at t = tcur[b] + 1 (learned initialisation);
+//   capture = 1: one row per (b, t <= Tend[b], i), row_base[b][t-1] + i, with
+//                the displacement target x_t^i - u (training data).
+struct ProposalRowsArgs {
+    ModelParams mp;
+    int B, Nmax, maxT, capture;
+    uint64_t seed;
+    const double* x0;             // [B][d]
+    const float* hist;            // [B][maxT][Nmax][d]
+    const float* y;               // [B][maxT][dy]
+    const int* tcur;              // [B]
+    const int* Tend;              // [B]
+    const int* Nseq;              // [B]
+    const long long* row_base;    // [B][maxT] (capture)
+    float* feat;                  // [rows][32]
+    float* u;                     // [rows][d] or null
+    float* targ;                  // [rows][16] or null (capture)
+};
+
+// Defined in smap_mlp.cu.
+smap_status proposal_launch_init(smap_proposal* p, const ProposalRowsArgs& ra, float* xinit, cudaStream_t st);
+smap_status proposal_launch_capture(smap_proposal* p, const ProposalRowsArgs& ra, cudaStream_t st);
+int proposal_kind(const smap_proposal* p);
+int proposal_d(const smap_proposal* p);
 
 // Shared by the ABI translation units (defined in smap_api.cu).
 extern std::atomic<uint64_t> g_launches;

@@ -32,7 +32,7 @@ constexpr float kLam = 1.3862943611198906f;    // 1 / kKm^2 = 2 ln 2
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct SmemLayout {
-    size_t phis, xs, gs, fs, cand, zs, red, misc, total;
+    size_t phis, xs, gs, fs, nrm, cand, zs, red, misc, total;
 };
 
 // Dynamic shared memory of the step kernels for Nmax particles of stride DP.
@@ -43,6 +43,7 @@ __host__ __device__ inline SmemLayout smem_layout(int Nmax, int DP) {
     L.xs = off;   off = align16(off + sizeof(float) * Nmax * DP);
     L.gs = off;   off = align16(off + sizeof(float) * Nmax * (DP < 2 ? 2 : DP));
     L.fs = off;   off = align16(off + sizeof(float) * Nmax * DP);
+    L.nrm = off;  off = align16(off + sizeof(float) * Nmax);
     L.cand = off; off = align16(off + sizeof(uint32_t) * kCandCap);
     L.zs = off;   off = align16(off + sizeof(float) * kMaxDy);
     L.red = off;  off = align16(off + sizeof(double) * 40);
@@ -54,8 +55,9 @@ __host__ __device__ inline SmemLayout smem_layout(int Nmax, int DP) {
 struct Sm {
     double* phis;   // phi_{t-1}(j), j < Np
     float* xs;      // particles [N][DP] (absolute, or centred+scaled inside SVGD)
-    float* gs;      // scores [N][DP]; later (A+, A-) pairs of the recursion screen
+    float* gs;      // w_k = A g_k - Bc x^_k [N][DP]; later (A+, A-) of the recursion screen
     float* fs;      // (f_t(x_{t-1}^j) - c) Q^-1/2 kKm, [Np][DP]
+    float* nrm;     // |x^_k|^2 of the scaled particles
     uint32_t* cand; // median candidates / histograms
     float* zs;      // observation z_t
     double* redd;   // reduction scratch (aliases redi / redf)
@@ -72,6 +74,7 @@ __device__ inline Sm bind_smem(unsigned char* base, int Nmax, int DP) {
     s.xs = reinterpret_cast<float*>(base + L.xs);
     s.gs = reinterpret_cast<float*>(base + L.gs);
     s.fs = reinterpret_cast<float*>(base + L.fs);
+    s.nrm = reinterpret_cast<float*>(base + L.nrm);
     s.cand = reinterpret_cast<uint32_t*>(base + L.cand);
     s.zs = reinterpret_cast<float*>(base + L.zs);
     s.redd = reinterpret_cast<double*>(base + L.red);
@@ -187,13 +190,16 @@ struct BracketCount {
     }
 };
 
-// 256-bin histogram of the key bits >> 18 (1/32 octave per bin), centred on a
-// guess; the two end bins collect the tails.
-struct LogHist {
-    int base;
+// 256-bin histogram of keys: bin = (key - key_lo) >> shift, clamped, so bin 0
+// and bin 255 also collect everything below and above the covered range.
+struct KeyHist {
+    uint32_t key_lo;
+    int shift;
     int* hist;
     __device__ __forceinline__ void operator()(float v) {
-        const int bin = min(max((int)(__float_as_uint(v) >> 18) - base, 0), 255);
+        const uint32_t key = __float_as_uint(v);
+        const uint32_t off = key >= key_lo ? (key - key_lo) >> shift : 0u;
+        const int bin = (int)min(off, 255u);
         const unsigned act = __activemask();
         const unsigned peers = __match_any_sync(act, bin);
         if ((int)lane_id() == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
@@ -272,7 +278,8 @@ __device__ bool bracket_pass(const Sm& s, int N, float lo, float hi, int r1, int
     const int nlo = block_sum_int(f.nlo, s.redi);   // ends with a barrier
     const int nc = *s.ncand;
     nc_out = nc;
-    bool ok = nlo <= r1 && r2 < nlo + nc && nc <= kCandCap;
+    const bool inside = nlo <= r1 && r2 < nlo + nc;
+    bool ok = inside && nc <= kCandCap;
     if (ok) {
         int n2 = 1;
         while (n2 < nc) n2 <<= 1;
@@ -282,6 +289,8 @@ __device__ bool bracket_pass(const Sm& s, int N, float lo, float hi, int r1, int
         v1 = s.cand[r1 - nlo];
         v2 = s.cand[r2 - nlo];
     }
+    __syncthreads();
+    if (threadIdx.x == 0) s.redi[39] = inside ? 1 : 0;
     __syncthreads();
     return ok;
 }
@@ -295,34 +304,90 @@ struct MedState {
     int fresh;     // the set changed beyond one SVGD update (new step)
 };
 
+// One histogram pass (KeyHist) that locates ranks r1 <= r2: on success
+// [lo, hi] is the key range of their bins, n_in the number of keys in it.
+template <int D, int DP>
+__device__ bool locate_pass(const Sm& s, int N, uint32_t key_lo, int shift, int r1, int r2, uint32_t& lo,
+                            uint32_t& hi, int& n_in) {
+    int* hist = reinterpret_cast<int*>(s.cand);
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    KeyHist f{key_lo, shift, hist};
+    for_each_pair<D, DP>(s.xs, N, f);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int cum = 0, b1 = -1, b2 = -1, c1 = 0, cnt = 0;
+        for (int bin = 0; bin < 256; ++bin) {
+            const int c = hist[bin];
+            if (b1 < 0 && cum + c > r1) { b1 = bin; c1 = cum; }
+            if (b1 >= 0) cnt += c;
+            if (cum + c > r2) { b2 = bin; break; }
+            cum += c;
+        }
+        s.redi[36] = b1;
+        s.redi[37] = b2;
+        s.redi[38] = cnt;
+        (void)c1;
+    }
+    __syncthreads();
+    const int b1 = s.redi[36], b2 = s.redi[37];
+    n_in = s.redi[38];
+    __syncthreads();
+    // the end bins also hold keys outside the covered range: not usable
+    if (b1 <= 0 || b2 >= 255 || b2 < b1) return false;
+    lo = key_lo + ((uint32_t)b1 << shift);
+    hi = key_lo + ((uint32_t)(b2 + 1) << shift) - 1u;
+    return true;
+}
+
+// Bracket [lo, hi] (keys) known to contain the middle ranks but too many
+// keys: a histogram of 256 bins over it, then the bracket of the located bins.
+template <int D, int DP>
+__device__ bool refine_pass(const Sm& s, int N, uint32_t lo, uint32_t hi, int r1, int r2, uint32_t& v1,
+                            uint32_t& v2, int& nc, float& width) {
+    int shift = 0;
+    while (shift < 31 && ((hi - lo) >> shift) >= 254u) ++shift;
+    uint32_t l2, h2;
+    int n2;
+    // key_lo one bin below lo keeps bin 0 for the keys under the range
+    const uint32_t klo = lo >= (1u << shift) ? lo - (1u << shift) : 0u;
+    if (!locate_pass<D, DP>(s, N, klo, shift, r1, r2, l2, h2, n2)) return false;
+    width = __uint_as_float(h2) - __uint_as_float(l2);
+    return bracket_pass<D, DP>(s, N, __uint_as_float(l2), __uint_as_float(h2), r1, r2, v1, v2, nc);
+}
+
 // Median of the squared pairwise distances of the particles in xs, whose
 // coordinates are scaled by sqrt(s2) (so scaled distances = s2 * true ones).
 // Returns the median in true units. Path: a tight bracket around the
 // extrapolated previous median (usual case); at a new step, a 256-bin
-// histogram over +-4 octaves locates the bracket first; an exact radix
-// select is the last resort. stats (may be null): [0] bracket hits,
-// [1] histogram locates, [2] radix fallbacks.
+// histogram over +-4 octaves of a guess locates the middle ranks (and a second
+// histogram over the located bins when they hold more than kCandCap keys); an
+// exact radix select is the last resort. stats (may be null): [0] bracket
+// hits, [1] histogram locates, [2] radix fallbacks.
 template <int D, int DP>
 __device__ float median_sqdist(const Sm& s, int N, float s2, float q_extra, MedState& st, int* stats) {
     const int P = N * (N - 1) / 2;
     const int r1 = (P & 1) ? (P - 1) / 2 : P / 2 - 1;
     const int r2 = (P & 1) ? r1 : P / 2;
+    const int target = 300;   // candidates a bracket aims at
     uint32_t v1 = 0, v2 = 0;
     int nc = 0, path = 2;
+    float width = 0.0f;       // key-value width of the bracket that succeeded
     bool done = false;
     if (st.have && !st.fresh) {
         const float g = st.med * st.trend * s2;
-        done = bracket_pass<D, DP>(s, N, g * (1.0f - st.w), g * (1.0f + st.w), r1, r2, v1, v2, nc);
+        const float lo = g * (1.0f - st.w), hi = g * (1.0f + st.w);
+        done = bracket_pass<D, DP>(s, N, lo, hi, r1, r2, v1, v2, nc);
+        width = hi - lo;
         if (done) {
             path = 0;
-            if (nc > 512) st.w *= 0.6f;
-            else if (nc < 48) st.w = fminf(st.w * 1.5f, 0.05f);
-        } else {
-            st.w = fminf(st.w * 2.0f, 0.05f);
+        } else if (nc > kCandCap && s.redi[39]) {
+            // the middle ranks are inside but the bracket is too wide
+            done = refine_pass<D, DP>(s, N, __float_as_uint(lo), __float_as_uint(hi), r1, r2, v1, v2, nc, width);
+            if (done) path = 1;
         }
     }
     if (!done) {
-        // locate the middle ranks in a 256-bin log histogram around a guess
         float g;
         if (st.have) {
             g = (st.med + q_extra) * s2;
@@ -343,30 +408,18 @@ __device__ float median_sqdist(const Sm& s, int N, float s2, float q_extra, MedS
             __syncthreads();
         }
         if (g > 0.0f && isfinite(g)) {
-            int* hist = reinterpret_cast<int*>(s.cand);
-            for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
-            __syncthreads();
-            LogHist f{(int)(__float_as_uint(g) >> 18) - 128, hist};
-            for_each_pair<D, DP>(s.xs, N, f);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                int cum = 0, b1 = -1, b2 = -1;
-                for (int bin = 0; bin < 256; ++bin) {
-                    const int c = hist[bin];
-                    if (b1 < 0 && cum + c > r1) b1 = bin;
-                    if (b2 < 0 && cum + c > r2) { b2 = bin; break; }
-                    cum += c;
+            // 1/32 octave per bin, +-4 octaves around g
+            const uint32_t gk = __float_as_uint(g);
+            const uint32_t klo = gk > (128u << 18) ? gk - (128u << 18) : 0u;
+            uint32_t lo, hi;
+            int n_in;
+            if (locate_pass<D, DP>(s, N, klo, 18, r1, r2, lo, hi, n_in)) {
+                if (n_in <= kCandCap) {
+                    done = bracket_pass<D, DP>(s, N, __uint_as_float(lo), __uint_as_float(hi), r1, r2, v1, v2, nc);
+                    width = __uint_as_float(hi) - __uint_as_float(lo);
+                } else {
+                    done = refine_pass<D, DP>(s, N, lo, hi, r1, r2, v1, v2, nc, width);
                 }
-                s.redi[36] = b1;
-                s.redi[37] = b2;
-            }
-            __syncthreads();
-            const int b1 = s.redi[36], b2 = s.redi[37];
-            __syncthreads();
-            if (b1 > 0 && b2 < 255 && b2 >= b1 && f.base + b1 >= 0) {
-                const uint32_t lo = (uint32_t)(f.base + b1) << 18;
-                const uint32_t hi = ((uint32_t)(f.base + b2 + 1) << 18) - 1u;
-                done = bracket_pass<D, DP>(s, N, __uint_as_float(lo), __uint_as_float(hi), r1, r2, v1, v2, nc);
                 if (done) path = 1;
             }
         }
@@ -376,10 +429,16 @@ __device__ float median_sqdist(const Sm& s, int N, float s2, float q_extra, MedS
         v2 = (r2 == r1) ? v1 : radix_select<D, DP>(s, N, r2);
     }
     if (stats && threadIdx.x == 0) atomicAdd(&stats[path], 1);
-    const float med = 0.5f * (__uint_as_float(v1) + __uint_as_float(v2)) / s2;
+    const float med_s = 0.5f * (__uint_as_float(v1) + __uint_as_float(v2));
+    const float med = med_s / s2;
     if (st.have && !st.fresh && st.med > 0.0f) st.trend = fminf(fmaxf(med / st.med, 0.8f), 1.25f);
     else st.trend = 1.0f;
-    if (st.fresh || !st.have) st.w = 0.004f;
+    // next bracket: the width that held nc keys, scaled to hold about `target`
+    if (done && nc > 0 && med_s > 0.0f)
+        st.w = fminf(fmaxf(0.5f * width / med_s * fminf(fmaxf((float)target / (float)nc, 0.25f), 4.0f),
+                           1e-6f), 0.05f);
+    else
+        st.w = 0.004f;
     st.med = med;
     st.have = 1;
     st.fresh = 0;
@@ -462,13 +521,16 @@ __device__ void prepare_step(const ModelParams& mp, const Sm& s, int t, int N, i
 }
 
 // ---------------------------------------------------------------------------
-// a4: scores g_i = grad log p(z_t | x_i) + grad log prior(x_i) -> gs, for the
-// block's particles held as x^ = (x - c) * sc in xs; each particle is first
-// rescaled by `rescale` (the new kernel scale over the old) and written back.
+// a4: scores g_i = grad log p(z_t | x_i) + grad log prior(x_i) for the block's
+// particles held as x^ = (x - c) * sc in xs; each particle is first rescaled
+// by `rescale` (the new kernel scale over the old) and written back. What is
+// stored is what the update needs: w_i = Aw g_i - Bw x^_i in gs and |x^_i|^2
+// in nrm (see rbf_update).
 // ---------------------------------------------------------------------------
 template <class M, int PPT>
 __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const Sm& s, int N, int Np,
-                                                  int prior, float rescale, float inv_sc) {
+                                                  int prior, float rescale, float inv_sc, float Aw,
+                                                  float Bw) {
     constexpr int D = M::D, DP = M::DP;
     const int tid = threadIdx.x, NT = blockDim.x;
     float xt[PPT][D], A[PPT][D], S[PPT], Mref[PPT];
@@ -566,59 +628,70 @@ __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const S
             for (int c = 0; c < D; ++c)
                 g[c] -= mp.sqrt_qinv_f[c] * (1.0f / kKm) * (xt[p][c] - s.misc[16 + c]);
         }
+        float n2 = 0.0f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            n2 = fmaf(xh[c], xh[c], n2);
+            g[c] = fmaf(Aw, g[c], -Bw * xh[c]);
+        }
         store_row<D, DP>(s.gs, i, g);
+        s.nrm[i] = n2;
     }
 }
 
 // ---------------------------------------------------------------------------
-// a5: one SVGD update (Eq. svgd_iterate) in the scaled coordinates:
-// kappa_ik = 2^-|x^_i - x^_k|^2, x^_i += A sum_k kappa g_k + Bc sum_k kappa (x^_i - x^_k)
-// with A = sc eps / N and Bc = 2 eps / (N h).
+// a5: one SVGD update (Eq. svgd_iterate) in the scaled coordinates, where
+// kappa_ik = 2^-|x^_i - x^_k|^2 and the update
+//   x^_i += A sum_k kappa_ik g_k + Bc sum_k kappa_ik (x^_i - x^_k)
+// (A = sc eps / N, Bc = 2 eps / (N h)) is regrouped as
+//   x^_i += sum_k kappa_ik w_k + Bc x^_i sum_k kappa_ik,   w_k = A g_k - Bc x^_k,
+// so a pair costs one dot product, one ex2 and d + 1 accumulations; the
+// distance is |x^_i|^2 + |x^_k|^2 - 2 x^_i . x^_k, well conditioned because the
+// coordinates are in units of the kernel width.
 // ---------------------------------------------------------------------------
 template <class M, int PPT>
-__device__ __forceinline__ void rbf_update(const Sm& s, int N, float A, float Bc) {
+__device__ __forceinline__ void rbf_update(const Sm& s, int N, float Bc) {
     constexpr int D = M::D, DP = M::DP;
     const int tid = threadIdx.x, NT = blockDim.x;
-    float xi[PPT][D], Sg[PPT][D], Sd[PPT][D];
+    float xi[PPT][D], ni[PPT], Sw[PPT][D], S0[PPT];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         const int i = min(tid + p * NT, N - 1);
         load_row<D, DP>(s.xs, i, xi[p]);
+        ni[p] = s.nrm[i];
+        S0[p] = 0.0f;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            Sg[p][c] = 0.0f;
-            Sd[p][c] = 0.0f;
+            xi[p][c] *= -2.0f;   // so that the dot product lands as -2 x^_i . x^_k
+            Sw[p][c] = 0.0f;
         }
     }
 #pragma unroll 2
     for (int k = 0; k < N; ++k) {
-        float xk[D], gk[D];
+        float xk[D], wk[D];
         load_row<D, DP>(s.xs, k, xk);
-        load_row<D, DP>(s.gs, k, gk);
+        load_row<D, DP>(s.gs, k, wk);
+        const float nk = s.nrm[k];
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
-            float diff[D], m = 0.0f;
+            float m = ni[p] + nk;
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
-                diff[c] = xi[p][c] - xk[c];
-                m = fmaf(diff[c], diff[c], m);
-            }
+            for (int c = 0; c < D; ++c) m = fmaf(xi[p][c], xk[c], m);
             const float kap = fast_exp2(-m);
+            S0[p] += kap;
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
-                Sg[p][c] = fmaf(kap, gk[c], Sg[p][c]);
-                Sd[p][c] = fmaf(kap, diff[c], Sd[p][c]);
-            }
+            for (int c = 0; c < D; ++c) Sw[p][c] = fmaf(kap, wk[c], Sw[p][c]);
         }
     }
-    __syncthreads();   // every thread is done reading xs / gs
+    __syncthreads();   // every thread is done reading xs / gs / nrm
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         const int i = tid + p * NT;
         if (i >= N) continue;
+        const float cx = -0.5f * Bc * S0[p];
         float xn[D];
 #pragma unroll
-        for (int c = 0; c < D; ++c) xn[c] = fmaf(A, Sg[p][c], fmaf(Bc, Sd[p][c], xi[p][c]));
+        for (int c = 0; c < D; ++c) xn[c] = fmaf(cx, xi[p][c], Sw[p][c] - 0.5f * xi[p][c]);
         store_row<D, DP>(s.xs, i, xn);
     }
     __syncthreads();
@@ -663,12 +736,12 @@ __device__ void svgd_iterations(const ModelParams& mp, const Sm& s, int N, int N
         }
         if (hout && tid == 0) hout[l] = h;
         const float sc_new = sqrtf(kL2E / h);
-        rescale_and_score<M, PPT>(mp, s, N, Np, prior, sc_new / sc, 1.0f / sc_new);
+        const float A = sc_new * eps / (float)N;
+        const float Bc = 2.0f * eps / ((float)N * h);
+        rescale_and_score<M, PPT>(mp, s, N, Np, prior, sc_new / sc, 1.0f / sc_new, A, Bc);
         sc = sc_new;
         __syncthreads();
-        const float A = sc * eps / (float)N;
-        const float Bc = 2.0f * eps / ((float)N * h);
-        rbf_update<M, PPT>(s, N, A, Bc);
+        rbf_update<M, PPT>(s, N, Bc);
     }
     // back to absolute coordinates
     const float inv = 1.0f / sc;
@@ -838,6 +911,7 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
         if (a.status[b] != 0) continue;
         const int N = a.Nseq[b];
         const int t0 = a.tcur[b];
+        if (a.mode == 1 && a.skip_done && t0 >= a.Tend[b]) continue;
         const int t1 = (a.mode == 1) ? t0 + 1 : a.Tend[b];
         if (t1 > a.maxT || N < 1 || N > a.Nmax) {
             if (tid == 0) a.status[b] = 1;
@@ -861,11 +935,11 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
         int tdone = t0;
         __syncthreads();
         for (int t = t0 + 1; t <= t1; ++t) {
-            const float* yt = (a.mode == 1) ? a.y + (size_t)b * mp.dy
-                                            : a.y + ((size_t)b * a.maxT + (t - 1)) * mp.dy;
+            const float* yt = (a.mode == 1 && !a.y_full) ? a.y + (size_t)b * mp.dy
+                                                         : a.y + ((size_t)b * a.maxT + (t - 1)) * mp.dy;
             const float* xin = a.viterbi_only
                                    ? a.hist + (((size_t)b * a.maxT + (t - 1)) * a.Nmax) * D
-                                   : nullptr;
+                                   : (a.xinit ? a.xinit + (size_t)b * a.Nmax * D : nullptr);
             prepare_step<M, PPT>(mp, s, t, N, Np, t == 1, a.x0 + (size_t)b * D, yt, f64, a.prior,
                                  a.seed, (uint32_t)b, xin);
             if (!a.viterbi_only) {

@@ -148,7 +148,7 @@ def clutter_params(dt=0.1, q=0.01, r=0.5, M=10, beta=0.2, area=100.0 * 100.0) ->
 
 
 def make_clutter_cv(B=4096, Tmin=50, Tmax=400, N=512, L=30, step=0.005, seed=3, M=10,
-                    p_miss=0.2, bw_value=1.0, prior=PRIOR_MIXTURE, uneven_N=None) -> Workload:
+                    p_miss=0.2, bw_value=1.0, prior=PRIOR_MIXTURE, uneven_N=None, first=0) -> Workload:
     p = clutter_params(M=M)
     dt, q, r = p[0], p[1], p[5]
     lengths = _rng(3, 888_888).integers(Tmin, Tmax + 1, B).astype(np.int32)
@@ -156,7 +156,7 @@ def make_clutter_cv(B=4096, Tmin=50, Tmax=400, N=512, L=30, step=0.005, seed=3, 
     x0 = np.zeros((B, 4)); y = np.full((B, maxT, 2 * M), np.nan, np.float32)
     truth = np.full((B, maxT + 1, 4), np.nan)
     for s in range(B):
-        g = _rng(3, s)
+        g = _rng(3, first + s)
         x = np.concatenate([g.uniform(-20.0, 20.0, 2), g.normal(0.0, 1.0, 2)])
         x0[s] = x
         truth[s, 0] = x
@@ -186,7 +186,7 @@ def _arm_fk(qang, lengths):
 
 
 def make_planar_arm(B=256, T=100, N=1024, L=50, step=1e-5, seed=4, nl=7, bw_value=1.0,
-                    prior=PRIOR_MIXTURE) -> Workload:
+                    prior=PRIOR_MIXTURE, first=0) -> Workload:
     p = arm_params(nl=nl)
     dt, r = p[0], p[2]
     qv = p[3: 3 + 2 * nl]
@@ -194,7 +194,7 @@ def make_planar_arm(B=256, T=100, N=1024, L=50, step=1e-5, seed=4, nl=7, bw_valu
     d = 2 * nl
     x0 = np.zeros((B, d)); y = np.zeros((B, T, 2), np.float32); truth = np.zeros((B, T + 1, d))
     for s in range(B):
-        g = _rng(4, s)
+        g = _rng(4, first + s)
         x = np.concatenate([g.uniform(-0.5, 0.5, nl), np.zeros(nl)])
         x0[s] = x
         truth[s, 0] = x

@@ -1,0 +1,194 @@
+"""The learned proposal on the GPU against the FP64 oracle.
+
+BF16 operands (weights, standardised inputs, hidden activations) with FP32
+accumulation against an FP64 network with the same BF16-rounded weights:
+outputs within 3e-2 of their spread, gradients within 5e-2 relative norm per
+parameter block. Training rows captured from a plain run must equal the
+oracle's recomputation (propagation, Philox noise, features). The gain test
+runs the method with and without the trained network at the same small L.
+"""
+import numpy as np
+import pytest
+
+from paper_2312_08684_gb300 import Estimator, _binding as abi, workloads as W
+
+pytestmark = pytest.mark.gpu
+H, INP, OUTP = 256, 32, 16
+
+
+@pytest.fixture(scope="module")
+def torch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    abi.load()
+    return torch
+
+
+def bf16(x):
+    x = np.ascontiguousarray(x, np.float32)
+    b = x.view(np.uint32)
+    r = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return r.astype(np.uint32).view(np.float32)
+
+
+def unpack(theta, n_in, n_out):
+    """Padded GPU layout -> the oracle's packed [W1, b1, W2, b2, W3, b3] (BF16 weights, FP32 biases)."""
+    o = 0
+    W1 = theta[o:o + H * INP].reshape(H, INP); o += H * INP
+    b1 = theta[o:o + H]; o += H
+    W2 = theta[o:o + H * H].reshape(H, H); o += H * H
+    b2 = theta[o:o + H]; o += H
+    W3 = theta[o:o + OUTP * H].reshape(OUTP, H); o += OUTP * H
+    b3 = theta[o:o + OUTP]
+    return np.concatenate([bf16(W1[:, :n_in]).ravel(), b1, bf16(W2).ravel(), b2,
+                           bf16(W3[:n_out]).ravel(), b3[:n_out]]).astype(np.float64)
+
+
+def _prop(torch, kind, params, seed=3):
+    p = abi.smap_proposal_create(kind, params, seed=seed)
+    n_in, n_out, hid, npar = abi.smap_proposal_dims(p)
+    assert hid == H
+    return p, n_in, n_out
+
+
+def test_forward_matches_oracle(oracle, torch):
+    p, n_in, n_out = _prop(torch, 4, W.arm_params())
+    try:
+        rng = np.random.default_rng(1)
+        theta, norm = abi.smap_proposal_get_weights(p)
+        norm[:n_in] = rng.normal(0, 1, n_in)
+        norm[INP:INP + n_in] = rng.uniform(0.5, 2.0, n_in)
+        norm[2 * INP:2 * INP + n_out] = rng.normal(0, 0.1, n_out)
+        norm[2 * INP + OUTP:2 * INP + OUTP + n_out] = rng.uniform(0.01, 0.1, n_out)
+        abi.smap_proposal_set_weights(p, theta, norm)
+        feat = np.zeros((300, INP), np.float32)
+        feat[:, :n_in] = rng.normal(0, 2, (300, n_in))
+        disp = torch.empty((300, n_out), dtype=torch.float32, device="cuda")
+        abi.smap_proposal_forward(p, torch.from_numpy(feat).cuda(), disp)
+        xn = bf16((feat[:, :n_in] - norm[:n_in]) / norm[INP:INP + n_in])
+        o = oracle.mlp_forward(n_in, H, n_out, unpack(theta, n_in, n_out), xn)
+        ref = o * norm[2 * INP + OUTP:2 * INP + OUTP + n_out] + norm[2 * INP:2 * INP + n_out]
+        got = disp.cpu().numpy()
+        spread = np.std(ref, axis=0).max()
+        assert np.max(np.abs(got - ref)) <= 3e-2 * spread
+    finally:
+        abi.smap_proposal_destroy(p)
+
+
+def test_gradient_matches_oracle(oracle, torch):
+    p, n_in, n_out = _prop(torch, 3, W.clutter_params())
+    try:
+        rng = np.random.default_rng(2)
+        R = 512
+        feat = np.zeros((R, INP), np.float32); feat[:, :n_in] = rng.normal(0, 1, (R, n_in))
+        targ = np.zeros((R, OUTP), np.float32); targ[:, :n_out] = rng.normal(0, 1, (R, n_out))
+        theta, norm = abi.smap_proposal_get_weights(p)     # identity normalisation
+        loss, g = abi.smap_proposal_loss_grad(p, torch.from_numpy(feat).cuda(), torch.from_numpy(targ).cuda())
+        Wp = unpack(theta, n_in, n_out)
+        lo, G = oracle.mlp_loss_grad(n_in, H, n_out, Wp, bf16(feat[:, :n_in]), targ[:, :n_out])
+        assert loss == pytest.approx(lo, rel=2e-2)
+        gp = np.concatenate([g[:H * INP].reshape(H, INP)[:, :n_in].ravel(), g[H * INP:H * INP + H],
+                             g[H * INP + H:H * INP + H + H * H], g[H * INP + H + H * H:H * INP + 2 * H + H * H],
+                             g[H * INP + 2 * H + H * H:H * INP + 2 * H + H * H + OUTP * H].reshape(OUTP, H)[:n_out].ravel(),
+                             g[-OUTP:][:n_out]])
+        sizes = [H * n_in, H, H * H, H, n_out * H, n_out]
+        o = 0
+        for k, s in enumerate(sizes):
+            a, b = gp[o:o + s], G[o:o + s]
+            assert np.linalg.norm(a - b) <= 5e-2 * np.linalg.norm(b), f"block {k}"
+            o += s
+        # padding stays untouched: zero gradient on the unused inputs / outputs
+        assert np.all(g[:H * INP].reshape(H, INP)[:, n_in:] == 0)
+    finally:
+        abi.smap_proposal_destroy(p)
+
+
+def test_training_fits_a_teacher(torch):
+    p, n_in, n_out = _prop(torch, 4, W.arm_params(), seed=5)
+    q, _, _ = _prop(torch, 4, W.arm_params(), seed=77)
+    try:
+        rng = np.random.default_rng(3)
+        R = 1 << 16
+        feat = np.zeros((R, INP), np.float32); feat[:, :n_in] = rng.normal(0, 1, (R, n_in))
+        fd = torch.from_numpy(feat).cuda()
+        disp = torch.empty((R, n_out), dtype=torch.float32, device="cuda")
+        abi.smap_proposal_forward(q, fd, disp)             # the teacher
+        targ = torch.zeros((R, OUTP), dtype=torch.float32, device="cuda")
+        targ[:, :n_out] = disp
+        abi.smap_proposal_fit_normalization(p, fd, targ)
+        curve = abi.smap_proposal_train(p, fd, targ, 600, 2048, 2e-3, 2e-4)
+        assert np.all(np.isfinite(curve))
+        assert np.mean(curve[-20:]) < 0.1 * np.mean(curve[:5])
+    finally:
+        abi.smap_proposal_destroy(p)
+        abi.smap_proposal_destroy(q)
+
+
+def test_capture_rows_match_oracle(oracle, torch):
+    wl = W.make_planar_arm(B=2, T=4, N=16, L=5)
+    p, n_in, n_out = _prop(torch, wl.kind, wl.params)
+    try:
+        with Estimator.from_workload(wl) as est:
+            est.run_batch(wl.y)
+            hist = est.history()
+            rows_max = wl.B * wl.maxT * wl.N
+            feat = torch.empty((rows_max, INP), dtype=torch.float32, device="cuda")
+            targ = torch.empty((rows_max, OUTP), dtype=torch.float32, device="cuda")
+            n = abi.smap_proposal_capture(p, est.h, feat, targ)
+        assert n == rows_max
+        feat, targ = feat.cpu().numpy(), targ.cpu().numpy()
+        m = oracle.Model(wl.kind, wl.params)
+        r = 0
+        for b in range(wl.B):
+            for t in range(1, wl.maxT + 1):
+                for i in range(wl.N):
+                    prev = wl.x0[b] if t == 1 else hist[b, t - 2, i].astype(np.float64)
+                    u = m.transition(t, prev) + np.sqrt(m.q) * oracle.normals(wl.seed, b, t, i, wl.d)
+                    f = oracle.proposal_features(wl.kind, wl.params, u, wl.y[b, t - 1].astype(np.float64))
+                    assert np.allclose(feat[r, :len(f)], f, rtol=1e-5, atol=2e-5)
+                    assert np.all(feat[r, len(f):] == 0)
+                    assert np.allclose(targ[r, :wl.d], hist[b, t - 1, i] - u, rtol=1e-4, atol=2e-6)
+                    r += 1
+    finally:
+        abi.smap_proposal_destroy(p)
+
+
+def _mean_J(wl, L, prop=None):
+    with Estimator.from_workload(wl, L=L) as est:
+        if prop is not None:
+            abi.smap_set_proposal(est.h, prop, L)
+        _, J = est.run_batch(wl.y, wl.T, wl.Nseq)
+    assert np.all(np.isfinite(J))
+    return float(np.mean(J))
+
+
+@pytest.mark.parametrize("which", ["arm", "clutter"])
+def test_learned_proposal_gains_over_plain_at_equal_iterations(torch, which):
+    """Train on plain L=50 runs, then compare the MAP log-posterior of the
+    learned initialisation + L=5 against plain L=5 (and plain L=50) on fresh
+    sequences: the network must close part of the gap."""
+    mk = {"arm": lambda B, s: W.make_planar_arm(B=B, T=30, N=256, L=50, seed=s),
+          "clutter": lambda B, s: W.make_clutter_cv(B=B, Tmin=30, Tmax=30, N=256, L=50, seed=s)}[which]
+    train_wl = mk(48, 11)
+    p, n_in, n_out = _prop(torch, train_wl.kind, train_wl.params, seed=9)
+    try:
+        rows = train_wl.B * train_wl.maxT * train_wl.N
+        feat = torch.empty((rows, INP), dtype=torch.float32, device="cuda")
+        targ = torch.empty((rows, OUTP), dtype=torch.float32, device="cuda")
+        with Estimator.from_workload(train_wl) as est:
+            est.run_batch(train_wl.y, train_wl.T, train_wl.Nseq)
+            n = abi.smap_proposal_capture(p, est.h, feat, targ)
+        abi.smap_proposal_fit_normalization(p, feat[:n], targ[:n])
+        curve = abi.smap_proposal_train(p, feat[:n], targ[:n], 1500, 4096, 1e-3, 1e-4)
+        assert np.mean(curve[-50:]) < 0.8 * np.mean(curve[:10])
+        # evaluation sequences are not among the training ones
+        ev = {"arm": lambda: W.make_planar_arm(B=32, T=30, N=256, L=5, first=1000),
+              "clutter": lambda: W.make_clutter_cv(B=32, Tmin=30, Tmax=30, N=256, L=5, first=1000)}[which]()
+        j5 = _mean_J(ev, 5)
+        jl = _mean_J(ev, 5, p)
+        j50 = _mean_J(ev, 50)
+        print(f"{which}: mean J plain L5 {j5:.2f}, learned L5 {jl:.2f}, plain L50 {j50:.2f}")
+        assert jl > j5
+    finally:
+        abi.smap_proposal_destroy(p)
