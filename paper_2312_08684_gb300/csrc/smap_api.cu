@@ -278,6 +278,9 @@ smap_status configure_kernel(smap_handle* h, const void* fn, size_t smem) {
         if (!flag) continue;
         if (!*flag) {
             SMAP_CUDA(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            // the whole unified L1 as shared memory: as many resident sequences as registers allow
+            SMAP_CUDA(h, cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                              (int)cudaSharedmemCarveoutMaxShared));
             *flag = true;
         }
         return SMAP_OK;
@@ -292,6 +295,7 @@ struct StepOpts {
     int y_full = 0;                 // y is [B][maxT][dy]
     int skip_done = 0;              // skip sequences with tcur >= Tend
     int L = -1;                     // SVGD iterations (-1: the handle's L)
+    const uint8_t* active = nullptr;  // per-sequence step mask [B] (smap_step)
 };
 
 // Launches the sequence kernel of variant v over `items` work items.
@@ -329,7 +333,7 @@ smap_status launch_seq(smap_handle* h, int v, int items, int mode, const float* 
     a.tcur = h->tcur;
     a.Nseq = h->Nseq;
     a.Tend = h->Tend;
-    a.active = (mode == 1) ? h->active : nullptr;
+    a.active = (mode == 1) ? opts.active : nullptr;
     a.order = order;
     a.f64 = h->f64;
     a.bwguess = h->bwguess;
@@ -769,7 +773,9 @@ smap_status smap_step(smap_handle* h, const float* y, const uint8_t* active, int
     SMAP_CUDA(h, cudaMemcpyAsync(h->active, h->active_h, h->B, cudaMemcpyHostToDevice, h->stream));
     SMAP_CUDA(h, cudaEventRecord(h->step_done, h->stream));
     const int v = h->variant >= 0 ? h->variant : heuristic_variant(h);
-    st = launch_seq(h, v, h->B, 1, h->ystep, 0, nullptr);
+    StepOpts so;
+    so.active = h->active;
+    st = launch_seq(h, v, h->B, 1, h->ystep, 0, nullptr, nullptr, nullptr, so);
     if (st) return st;
     for (int b = 0; b < h->B; ++b)
         if (h->active_h[b]) h->tcur_h[b] += 1;

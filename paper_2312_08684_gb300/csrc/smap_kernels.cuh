@@ -280,7 +280,23 @@ __device__ bool bracket_pass(const Sm& s, int N, float lo, float hi, int r1, int
     nc_out = nc;
     const bool inside = nlo <= r1 && r2 < nlo + nc;
     bool ok = inside && nc <= kCandCap;
-    if (ok) {
+    if (ok && nc <= 256) {
+        // rank of each candidate by counting (ties by position): one barrier
+        const int k1 = r1 - nlo, k2 = r2 - nlo;
+        for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+            const uint32_t key = s.cand[c];
+            int rank = 0;
+            for (int o = 0; o < nc; ++o) {
+                const uint32_t v = s.cand[o];
+                rank += (v < key) | ((v == key) & (o < c));
+            }
+            if (rank == k1) s.redi[40] = (int)key;
+            if (rank == k2) s.redi[41] = (int)key;
+        }
+        __syncthreads();
+        v1 = (uint32_t)s.redi[40];
+        v2 = (uint32_t)s.redi[41];
+    } else if (ok) {
         int n2 = 1;
         while (n2 < nc) n2 <<= 1;
         for (int i = nc + threadIdx.x; i < n2; i += blockDim.x) s.cand[i] = 0xFFFFFFFFu;
@@ -369,7 +385,7 @@ __device__ float median_sqdist(const Sm& s, int N, float s2, float q_extra, MedS
     const int P = N * (N - 1) / 2;
     const int r1 = (P & 1) ? (P - 1) / 2 : P / 2 - 1;
     const int r2 = (P & 1) ? r1 : P / 2;
-    const int target = 300;   // candidates a bracket aims at
+    const int target = 128;   // candidates a bracket aims at
     uint32_t v1 = 0, v2 = 0;
     int nc = 0, path = 2;
     float width = 0.0f;       // key-value width of the bracket that succeeded
@@ -557,10 +573,10 @@ __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const S
         // reference logit: the particle's own parent in the previous set
         float fr[D];
         load_row<D, DP>(s.fs, Np == 1 ? 0 : min(ii, Np - 1), fr);
-        Mref[p] = -sqdist<D>(xt[p], fr);
+        Mref[p] = sqdist<D>(xt[p], fr);
     }
     if (prior == 0) {
-        // mixture responsibilities w_ij = 2^-(|x~_i - f~_j|^2 + Mref) / sum:
+        // mixture responsibilities w_ij = 2^(Mref - |x~_i - f~_j|^2) / sum:
         // the parent's term is 1, so the sum is >= 1; a sum above 2^100 (a
         // far better component than the parent) is redone with the true max
         for (int j = 0; j < Np; ++j) {
@@ -572,9 +588,9 @@ __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const S
 #pragma unroll
                 for (int c = 0; c < D; ++c) {
                     diff[c] = xt[p][c] - fj[c];
-                    m = fmaf(diff[c], diff[c], m);
+                    m = fmaf(-diff[c], diff[c], m);
                 }
-                const float e = fast_exp2(-m);
+                const float e = fast_exp2(m);
                 S[p] += e;
 #pragma unroll
                 for (int c = 0; c < D; ++c) A[p][c] = fmaf(e, diff[c], A[p][c]);
@@ -658,11 +674,11 @@ __device__ __forceinline__ void rbf_update(const Sm& s, int N, float Bc) {
     for (int p = 0; p < PPT; ++p) {
         const int i = min(tid + p * NT, N - 1);
         load_row<D, DP>(s.xs, i, xi[p]);
-        ni[p] = s.nrm[i];
+        ni[p] = -s.nrm[i];
         S0[p] = 0.0f;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            xi[p][c] *= -2.0f;   // so that the dot product lands as -2 x^_i . x^_k
+            xi[p][c] *= 2.0f;   // the dot product then lands as 2 x^_i . x^_k
             Sw[p][c] = 0.0f;
         }
     }
@@ -674,10 +690,10 @@ __device__ __forceinline__ void rbf_update(const Sm& s, int N, float Bc) {
         const float nk = s.nrm[k];
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
-            float m = ni[p] + nk;
+            float m = ni[p] - nk;   // accumulates -|x^_i - x^_k|^2
 #pragma unroll
             for (int c = 0; c < D; ++c) m = fmaf(xi[p][c], xk[c], m);
-            const float kap = fast_exp2(-m);
+            const float kap = fast_exp2(m);
             S0[p] += kap;
 #pragma unroll
             for (int c = 0; c < D; ++c) Sw[p][c] = fmaf(kap, wk[c], Sw[p][c]);
@@ -688,10 +704,10 @@ __device__ __forceinline__ void rbf_update(const Sm& s, int N, float Bc) {
     for (int p = 0; p < PPT; ++p) {
         const int i = tid + p * NT;
         if (i >= N) continue;
-        const float cx = -0.5f * Bc * S0[p];
+        const float cx = 0.5f * fmaf(Bc, S0[p], 1.0f);
         float xn[D];
 #pragma unroll
-        for (int c = 0; c < D; ++c) xn[c] = fmaf(cx, xi[p][c], Sw[p][c] - 0.5f * xi[p][c]);
+        for (int c = 0; c < D; ++c) xn[c] = fmaf(cx, xi[p][c], Sw[p][c]);
         store_row<D, DP>(s.xs, i, xn);
     }
     __syncthreads();

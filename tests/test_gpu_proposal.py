@@ -158,8 +158,13 @@ def _mean_J(wl, L, prop=None):
     with Estimator.from_workload(wl, L=L) as est:
         if prop is not None:
             abi.smap_set_proposal(est.h, prop, L)
-        _, J = est.run_batch(wl.y, wl.T, wl.Nseq)
+        path, J = est.run_batch(wl.y, wl.T, wl.Nseq)
+        steps = np.empty(wl.B, np.int32)
+        abi.smap_get_steps(est.h, steps)
+    # every sequence ran all its steps and ended with a finite score
+    assert np.array_equal(steps, wl.T)
     assert np.all(np.isfinite(J))
+    assert np.all(np.isfinite(path[np.arange(wl.B), wl.T]))
     return float(np.mean(J))
 
 
