@@ -199,10 +199,11 @@ smap_status smap_viterbi_noalloc(int model, const double* params, int n_params, 
  * accumulation, maps a propagated particle u = f_t(x_{t-1}^i) + Q^{1/2} xi
  * (the plain initialisation) and the observation z_t to the displacement that
  * plain SVGD applies to it; the learned step then starts from u + MLP(u, z_t)
- * and runs a few SVGD iterations. Features (at most 32 per row, zero padded):
- *   PLANAR_ARM   [u, z, z - h(u)]
- *   CLUTTER_CV2D [velocity, the M points relative to the position, nearest first]
- *   others       [u, z (unheard = 0), heard flags]
+ * and runs a few SVGD iterations. Features (at most 32 per row, zero padded),
+ * each list ending with the likelihood score g = grad_u log p(z_t | u):
+ *   PLANAR_ARM   [u, z, z - h(u), g of the angles]
+ *   CLUTTER_CV2D [velocity, the M points relative to the position, nearest first, g of the position]
+ *   others       [u, z (unheard = 0), heard flags, g]
  * Training data rows are [32] FP32 features and [16] FP32 displacement targets
  * (zero padded). Parameters: FP32 master vector, padded layout W1 [256][32],
  * b1 [256], W2 [256][256], b2 [256], W3 [16][256], b3 [16]; normalisation

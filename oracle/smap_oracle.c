@@ -845,10 +845,11 @@ void om_adam(long n, double* theta, const double* g, double* m, double* v, int t
     }
 }
 
-/* Proposal features of a propagated particle u and observation z (at most 32):
- *   PLANAR_ARM   [u, z, z - h(u)]
- *   CLUTTER_CV2D [velocity, z_m - position for the points nearest first]
- *   others       [u, z with NaN -> 0, 1 where z is a number]
+/* Proposal features of a propagated particle u and observation z (at most 32),
+ * each list ending with the likelihood score g = grad_u log p(z | u):
+ *   PLANAR_ARM   [u, z, z - h(u), g of the angles]
+ *   CLUTTER_CV2D [velocity, z_m - position for the points nearest first, g of the position]
+ *   others       [u, z with NaN -> 0, 1 where z is a number, g]
  * Returns the count. */
 int om_proposal_features(int kind, const double* params, int np, const double* u, const double* z,
                          double* f)
@@ -856,14 +857,17 @@ int om_proposal_features(int kind, const double* params, int np, const double* u
     om_model m;
     if (om_setup(&m, kind, params, np)) return -1;
     int d = m.d, n = 0;
+    double g[OM_MAXD];
+    om_grad_loglik(&m, 1, z, u, g);
     if (kind == OM_PLANAR_ARM) {
         double e[2];
         om_arm_fk(&m, u, e, NULL);
         for (int c = 0; c < d; ++c) f[n++] = u[c];
         f[n++] = z[0]; f[n++] = z[1];
         f[n++] = z[0] - e[0]; f[n++] = z[1] - e[1];
+        for (int c = 0; c < d / 2; ++c) f[n++] = g[c];
     } else if (kind == OM_CLUTTER_CV2D) {
-        int M = (int)m.p[6], nm = M < 15 ? M : 15;
+        int M = (int)m.p[6], nm = M < 14 ? M : 14;
         double dist[32];
         int used[32] = {0};
         f[n++] = u[2]; f[n++] = u[3];
@@ -879,11 +883,13 @@ int om_proposal_features(int kind, const double* params, int np, const double* u
             f[n++] = z[2 * best] - u[0];
             f[n++] = z[2 * best + 1] - u[1];
         }
+        f[n++] = g[0]; f[n++] = g[1];
     } else {
-        int dy = m.dy < (32 - d) / 2 ? m.dy : (32 - d) / 2;
+        int dy = m.dy < (32 - 2 * d) / 2 ? m.dy : (32 - 2 * d) / 2;
         for (int c = 0; c < d; ++c) f[n++] = u[c];
         for (int c = 0; c < dy; ++c) f[n++] = isnan(z[c]) ? 0.0 : z[c];
         for (int c = 0; c < dy; ++c) f[n++] = isnan(z[c]) ? 0.0 : 1.0;
+        for (int c = 0; c < d; ++c) f[n++] = g[c];
     }
     return n;
 }

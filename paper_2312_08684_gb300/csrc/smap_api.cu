@@ -245,6 +245,8 @@ struct smap_handle {
     float* lfeat = nullptr;    // [B][Nmax][32]
     float* lu = nullptr;       // [B][Nmax][d]
     float* lxinit = nullptr;   // [B][Nmax][d]
+    cudaStream_t side = nullptr;   // second chain of the learned launches
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 };
 
 namespace {
@@ -296,6 +298,10 @@ struct StepOpts {
     int skip_done = 0;              // skip sequences with tcur >= Tend
     int L = -1;                     // SVGD iterations (-1: the handle's L)
     const uint8_t* active = nullptr;  // per-sequence step mask [B] (smap_step)
+    int seq_base = 0;               // items are sequences seq_base .. seq_base + items - 1
+    int queue_slot = 0;             // work-queue counter (one per concurrent launch)
+    double* f64 = nullptr;          // FP64 scratch of this launch (default: the handle's)
+    cudaStream_t stream = nullptr;  // launch stream (default: the handle's)
 };
 
 // Launches the sequence kernel of variant v over `items` work items.
@@ -335,18 +341,21 @@ smap_status launch_seq(smap_handle* h, int v, int items, int mode, const float* 
     a.Tend = h->Tend;
     a.active = (mode == 1) ? opts.active : nullptr;
     a.order = order;
-    a.f64 = h->f64;
+    a.f64 = opts.f64 ? opts.f64 : h->f64;
     a.bwguess = h->bwguess;
     a.status = h->status;
-    a.queue = h->queue;
+    a.stats = h->status + h->B;
+    a.queue = h->queue + opts.queue_slot;
     a.viterbi_only = viterbi_only;
     a.xinit = opts.xinit;
     a.y_full = opts.y_full;
     a.skip_done = opts.skip_done;
+    a.seq_base = opts.seq_base;
     if (opts.L >= 0) a.L = opts.L;
     void* args[] = {&a};
-    SMAP_CUDA(h, cudaMemsetAsync(h->queue, 0, sizeof(int), h->stream));
-    SMAP_CUDA(h, cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, smem, h->stream));
+    cudaStream_t ls = opts.stream ? opts.stream : h->stream;
+    SMAP_CUDA(h, cudaMemsetAsync(a.queue, 0, sizeof(int), ls));
+    SMAP_CUDA(h, cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, smem, ls));
     SMAP_CUDA(h, cudaGetLastError());
     g_launches.fetch_add(1);
     h->last_threads = nt;
@@ -436,26 +445,42 @@ smap_status batch_device_work(smap_handle* h, int v) {
     if (st) return st;
     if (h->prop) {
         // learned initialisation: per step, rows (u, features) -> MLP -> one
-        // step of L_learned SVGD iterations for every unfinished sequence
-        ProposalRowsArgs ra;
-        memset(&ra, 0, sizeof(ra));
-        ra.mp = h->mp;
-        ra.B = h->B; ra.Nmax = h->Nmax; ra.maxT = h->maxT; ra.capture = 0;
-        ra.seed = h->cfg.seed;
-        ra.x0 = h->x0; ra.hist = h->hist; ra.y = h->y;
-        ra.tcur = h->tcur; ra.Tend = h->Tend; ra.Nseq = h->Nseq;
-        ra.feat = h->lfeat; ra.u = h->lu;
-        StepOpts so;
-        so.xinit = h->lxinit;
-        so.y_full = 1;
-        so.skip_done = 1;
-        so.L = h->L_learned;
-        for (int t = 1; t <= h->maxT; ++t) {
-            st = proposal_launch_init(h->prop, ra, h->lxinit, h->stream);
-            if (st) return fail(h, st, smap_proposal_last_error(h->prop));
-            st = launch_seq(h, v, h->B, 1, h->y, 0, h->order, nullptr, nullptr, so);
-            if (st) return st;
+        // step of L_learned SVGD iterations for every unfinished sequence. The
+        // batch is split into two independent chains on two streams, so one
+        // half's network and step tail overlap the other half's step kernel.
+        const int nch = h->B >= 2 ? 2 : 1;
+        SMAP_CUDA(h, cudaEventRecord(h->fork_ev, h->stream));
+        SMAP_CUDA(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
+        for (int c = 0; c < nch; ++c) {
+            const int b0 = (int)((long)h->B * c / nch), b1 = (int)((long)h->B * (c + 1) / nch);
+            cudaStream_t cs = c == 0 ? h->stream : h->side;
+            const size_t r0 = (size_t)b0 * h->Nmax;
+            ProposalRowsArgs ra;
+            memset(&ra, 0, sizeof(ra));
+            ra.mp = h->mp;
+            ra.B = b1 - b0; ra.b_base = b0; ra.Nmax = h->Nmax; ra.maxT = h->maxT; ra.capture = 0;
+            ra.seed = h->cfg.seed;
+            ra.x0 = h->x0; ra.hist = h->hist; ra.y = h->y;
+            ra.tcur = h->tcur; ra.Tend = h->Tend; ra.Nseq = h->Nseq;
+            ra.feat = h->lfeat + r0 * 32; ra.u = h->lu + r0 * h->d;
+            StepOpts so;
+            so.xinit = h->lxinit;
+            so.y_full = 1;
+            so.skip_done = 1;
+            so.L = h->L_learned;
+            so.seq_base = b0;
+            so.queue_slot = c;
+            so.f64 = h->f64 + r0 * h->d;
+            so.stream = cs;
+            for (int t = 1; t <= h->maxT; ++t) {
+                st = proposal_launch_init(h->prop, ra, h->lxinit + r0 * h->d, cs);
+                if (st) return fail(h, st, smap_proposal_last_error(h->prop));
+                st = launch_seq(h, v, b1 - b0, 1, h->y, 0, nullptr, nullptr, nullptr, so);
+                if (st) return st;
+            }
         }
+        SMAP_CUDA(h, cudaEventRecord(h->join_ev, h->side));
+        SMAP_CUDA(h, cudaStreamWaitEvent(h->stream, h->join_ev, 0));
     } else {
         st = launch_seq(h, v, h->B, 0, h->y, 0, h->order);
         if (st) return st;
@@ -503,6 +528,9 @@ smap_status smap_set_proposal(smap_handle* h, smap_proposal* p, int L_learned) {
             cudaGetLastError();
             return fail(h, SMAP_E_NOMEM, "learned-step buffers");
         }
+        SMAP_CUDA(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        SMAP_CUDA(h, cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+        SMAP_CUDA(h, cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
     }
     h->prop = p;
     h->L_learned = L_learned;
@@ -583,6 +611,9 @@ void smap_destroy(smap_handle* h) {
     if (h->step_done) cudaEventDestroy(h->step_done);
     for (void* q : {(void*)h->lfeat, (void*)h->lu, (void*)h->lxinit})
         if (q) cudaFree(q);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->join_ev) cudaEventDestroy(h->join_ev);
     for (cudaEvent_t ev : h->ev)
         if (ev) cudaEventDestroy(ev);
     if (h->ystep_h) cudaFreeHost(h->ystep_h);

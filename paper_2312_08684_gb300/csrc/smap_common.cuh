@@ -50,10 +50,12 @@ struct SeqArgs {
     float* bwguess;           // [B] last median of squared distances (scratch)
     int* status;              // [B] per-sequence status (0 or an smap_status)
     int* queue;               // [1] work-queue head
+    int* stats;               // [3] median-path counters (shared by all launches of a handle)
     int viterbi_only;         // 1: particle sets are given in hist (no SVGD)
     const float* xinit;       // mode 1: [B][Nmax][d] initial particles of the step, or null
     int y_full;               // mode 1: y is [B][maxT][dy] (indexed by the step)
     int skip_done;            // mode 1: skip sequences with tcur >= Tend
+    int seq_base;             // without `order`, item k is sequence seq_base + k
 };
 
 // Arguments of the debug SVGD kernel.

@@ -37,6 +37,7 @@ ModelKernels kernels_linear_gauss();
 struct ProposalRowsArgs {
     ModelParams mp;
     int B, Nmax, maxT, capture;
+    int b_base;                   // learned initialisation: rows are sequences b_base .. b_base + B - 1
     uint64_t seed;
     const double* x0;             // [B][d]
     const float* hist;            // [B][maxT][Nmax][d]

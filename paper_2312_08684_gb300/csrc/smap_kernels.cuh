@@ -922,7 +922,7 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
         __syncthreads();
         const int item = s_item;
         if (item >= a.B) break;
-        const int b = a.order ? a.order[item] : item;
+        const int b = a.order ? a.order[item] : a.seq_base + item;
         if (a.mode == 1 && a.active && !a.active[b]) continue;
         if (a.status[b] != 0) continue;
         const int N = a.Nseq[b];
@@ -961,7 +961,7 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
             if (!a.viterbi_only) {
                 st.fresh = 1;
                 svgd_iterations<M, PPT>(mp, s, N, Np, a.L, a.eps, a.bw_rule, a.bw_value, a.prior, st,
-                                        q_extra, nullptr, a.status + a.B);
+                                        q_extra, nullptr, a.stats);
             }
             int best[PPT];
             double phinew[PPT];

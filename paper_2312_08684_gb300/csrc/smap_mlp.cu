@@ -1,7 +1,8 @@
 // smap_mlp.cu -- kernels and C ABI of the learned proposal (smap_proposal_*).
 //
-// Forward: one fused kernel, weights resident in shared memory as BF16, 32-row
-// tiles through three mma.sync layers with GELU, FP32 accumulation.
+// Forward: one fused kernel, weights resident in shared memory as BF16 (the
+// 256-wide arrays XOR-swizzled instead of padded), 64-row tiles through three
+// mma.sync layers with GELU, FP32 accumulation.
 // Backward: a tiled BF16 GEMM (split-K for the weight gradients), GELU
 // derivative fused into its epilogue, column sums for the bias gradients.
 // Update: Adam on FP32 master weights, BF16 copies refreshed each step.
@@ -43,42 +44,56 @@ struct MlpFwdArgs {
     float* xout;                  // optional [rows][d]: u + displacement (physical units)
 };
 
-constexpr int kLdIn = kMlpInP + kMlpPad;
-constexpr int kLdH = kMlpH + kMlpPad;
+constexpr int kLdIn = kMlpInP + kMlpPad;   // padded row of the 32-wide arrays (W1, X)
+constexpr int kFwdRows = 64;                 // rows per tile of the fused forward
+
+// Element index in a 256-wide bf16 array whose 16-byte chunks are XOR-swizzled
+// by the row (chunk q of row r lives at q ^ (r & 7)): ldmatrix on 8 rows at the
+// same logical chunk touches 8 different bank groups.
+__device__ __forceinline__ int swz256(int r, int c) { return r * kMlpH + ((((c >> 3) ^ (r & 7))) << 3) + (c & 7); }
 
 __host__ __device__ inline size_t mlp_fwd_smem() {
-    return sizeof(bf16) * ((size_t)kMlpH * kLdIn + (size_t)kMlpH * kLdH + (size_t)kMlpOutP * kLdH +
-                           (size_t)kMlpRows * kLdIn + 2 * (size_t)kMlpRows * kLdH) +
+    return sizeof(bf16) * ((size_t)kMlpH * kLdIn +          // W1
+                           (size_t)kMlpH * kMlpH +          // W2 (swizzled)
+                           (size_t)kMlpOutP * kMlpH +       // W3 (swizzled)
+                           (size_t)kFwdRows * kMlpH +       // H1 (swizzled)
+                           (size_t)kFwdRows * kMlpH) +      // H2 (swizzled), X aliased at its start
            sizeof(float) * (2 * kMlpH + kMlpOutP + 2 * kMlpInP + 2 * kMlpOutP);
 }
 
-// One hidden layer for the 32-row tile: warp w computes columns [32w, 32w+32).
+// One hidden layer for the 64-row tile: warp w computes columns [32w, 32w+32)
+// of all 64 rows (4 x 4 MMA tiles). A is the padded 32-wide input (layer 1) or
+// a swizzled 256-wide activation (layer 2); W likewise.
 template <int K>
-__device__ __forceinline__ void mlp_hidden(const bf16* sA, int lda, const bf16* sW, int ldw, const float* bias,
-                                           bf16* sOut, int ldo, float* zg, bf16* hg, long row0, long rows) {
+__device__ __forceinline__ void mlp_hidden(const bf16* sA, const bf16* sW, const float* bias, bf16* sOut,
+                                           float* zg, bf16* hg, long row0, long rows) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n0 = warp * 32;
-    float acc[2][4][4];
+    float acc[4][4][4];
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+    for (int mt = 0; mt < 4; ++mt)
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
     const int q = lane >> 3, r8 = lane & 7;
-#pragma unroll 4
+#pragma unroll 2
     for (int kk = 0; kk < K; kk += 16) {
-        uint32_t a[2][4];
+        uint32_t a[4][4];
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-            ldsm_x4(smem_addr(sA + (mt * 16 + (q & 1) * 8 + r8) * lda + kk + (q >> 1) * 8), a[mt][0], a[mt][1],
-                    a[mt][2], a[mt][3]);
+        for (int mt = 0; mt < 4; ++mt) {
+            const int r = mt * 16 + (q & 1) * 8 + r8, c = kk + (q >> 1) * 8;
+            const bf16* pa = (K == kMlpH) ? sA + swz256(r, c) : sA + r * kLdIn + c;
+            ldsm_x4(smem_addr(pa), a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+        }
 #pragma unroll
         for (int np = 0; np < 2; ++np) {
+            const int r = n0 + np * 16 + (q >> 1) * 8 + r8, c = kk + (q & 1) * 8;
+            const bf16* pw = (K == kMlpH) ? sW + swz256(r, c) : sW + r * kLdIn + c;
             uint32_t b0, b1, b2, b3;
-            ldsm_x4(smem_addr(sW + (n0 + np * 16 + (q >> 1) * 8 + r8) * ldw + kk + (q & 1) * 8), b0, b1, b2, b3);
+            ldsm_x4(smem_addr(pw), b0, b1, b2, b3);
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
+            for (int mt = 0; mt < 4; ++mt) {
                 mma_16816(acc[mt][2 * np], a[mt], b0, b1);
                 mma_16816(acc[mt][2 * np + 1], a[mt], b2, b3);
             }
@@ -86,7 +101,7 @@ __device__ __forceinline__ void mlp_hidden(const bf16* sA, int lda, const bf16* 
     }
     const int g = lane >> 2, tq = lane & 3;
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+    for (int mt = 0; mt < 4; ++mt)
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
@@ -95,11 +110,10 @@ __device__ __forceinline__ void mlp_hidden(const bf16* sA, int lda, const bf16* 
                 const int c = n0 + nt * 8 + 2 * tq;
                 const float za = acc[mt][nt][2 * hh] + bias[c];
                 const float zb = acc[mt][nt][2 * hh + 1] + bias[c + 1];
-                const bf16 ha = __float2bfloat16(gelu_f(za)), hb = __float2bfloat16(gelu_f(zb));
                 __nv_bfloat162 pr;
-                pr.x = ha;
-                pr.y = hb;
-                *reinterpret_cast<__nv_bfloat162*>(sOut + r * ldo + c) = pr;
+                pr.x = __float2bfloat16(gelu_f(za));
+                pr.y = __float2bfloat16(gelu_f(zb));
+                *reinterpret_cast<__nv_bfloat162*>(sOut + swz256(r, c)) = pr;
                 const long gr = row0 + r;
                 if (gr < rows) {
                     if (zg) *reinterpret_cast<float2*>(zg + gr * kMlpH + c) = make_float2(za, zb);
@@ -112,11 +126,11 @@ __global__ void __launch_bounds__(256, 1) mlp_forward_kernel(const __grid_consta
     extern __shared__ __align__(16) unsigned char smraw[];
     bf16* sW1 = reinterpret_cast<bf16*>(smraw);
     bf16* sW2 = sW1 + kMlpH * kLdIn;
-    bf16* sW3 = sW2 + kMlpH * kLdH;
-    bf16* sX = sW3 + kMlpOutP * kLdH;
-    bf16* sH1 = sX + kMlpRows * kLdIn;
-    bf16* sH2 = sH1 + kMlpRows * kLdH;
-    float* sb1 = reinterpret_cast<float*>(sH2 + kMlpRows * kLdH);
+    bf16* sW3 = sW2 + kMlpH * kMlpH;
+    bf16* sH1 = sW3 + kMlpOutP * kMlpH;
+    bf16* sH2 = sH1 + kFwdRows * kMlpH;
+    bf16* sX = sH2;   // the input tile is dead once layer 1 has run
+    float* sb1 = reinterpret_cast<float*>(sH2 + kFwdRows * kMlpH);
     float* sb2 = sb1 + kMlpH;
     float* sb3 = sb2 + kMlpH;
     float* snorm = sb3 + kMlpOutP;   // mu_in, sd_in, mu_out, sd_out
@@ -124,9 +138,12 @@ __global__ void __launch_bounds__(256, 1) mlp_forward_kernel(const __grid_consta
     for (int e = tid; e < kMlpH * kMlpInP; e += blockDim.x) sW1[(e / kMlpInP) * kLdIn + e % kMlpInP] = a.W1[e];
     for (int e = tid; e < kMlpH * kMlpH / 8; e += blockDim.x) {
         const int r = (e * 8) / kMlpH, c = (e * 8) % kMlpH;
-        *reinterpret_cast<uint4*>(sW2 + r * kLdH + c) = reinterpret_cast<const uint4*>(a.W2)[e];
+        *reinterpret_cast<uint4*>(sW2 + swz256(r, c)) = reinterpret_cast<const uint4*>(a.W2)[e];
     }
-    for (int e = tid; e < kMlpOutP * kMlpH; e += blockDim.x) sW3[(e / kMlpH) * kLdH + e % kMlpH] = a.W3[e];
+    for (int e = tid; e < kMlpOutP * kMlpH / 8; e += blockDim.x) {
+        const int r = (e * 8) / kMlpH, c = (e * 8) % kMlpH;
+        *reinterpret_cast<uint4*>(sW3 + swz256(r, c)) = reinterpret_cast<const uint4*>(a.W3)[e];
+    }
     for (int e = tid; e < kMlpH; e += blockDim.x) { sb1[e] = a.b1[e]; sb2[e] = a.b2[e]; }
     for (int e = tid; e < kMlpOutP; e += blockDim.x) sb3[e] = a.b3[e];
     for (int e = tid; e < 2 * kMlpInP + 2 * kMlpOutP; e += blockDim.x) snorm[e] = a.norm[e];
@@ -136,9 +153,9 @@ __global__ void __launch_bounds__(256, 1) mlp_forward_kernel(const __grid_consta
     const float* mu_out = snorm + 2 * kMlpInP;
     const float* sd_out = mu_out + kMlpOutP;
     const int warp = tid >> 5, lane = tid & 31;
-    for (long tile = blockIdx.x; tile * kMlpRows < a.rows; tile += gridDim.x) {
-        const long row0 = tile * kMlpRows;
-        for (int e = tid; e < kMlpRows * kMlpInP; e += blockDim.x) {
+    for (long tile = blockIdx.x; tile * kFwdRows < a.rows; tile += gridDim.x) {
+        const long row0 = tile * kFwdRows;
+        for (int e = tid; e < kFwdRows * kMlpInP; e += blockDim.x) {
             const int r = e / kMlpInP, c = e % kMlpInP;
             const long gr = row0 + r;
             float v = 0.0f;
@@ -151,20 +168,20 @@ __global__ void __launch_bounds__(256, 1) mlp_forward_kernel(const __grid_consta
             if (a.xn && gr < a.rows) a.xn[gr * kMlpInP + c] = bv;
         }
         __syncthreads();
-        mlp_hidden<kMlpInP>(sX, kLdIn, sW1, kLdIn, sb1, sH1, kLdH, a.z1, a.h1, row0, a.rows);
+        mlp_hidden<kMlpInP>(sX, sW1, sb1, sH1, a.z1, a.h1, row0, a.rows);
         __syncthreads();
-        mlp_hidden<kMlpH>(sH1, kLdH, sW2, kLdH, sb2, sH2, kLdH, a.z2, a.h2, row0, a.rows);
+        mlp_hidden<kMlpH>(sH1, sW2, sb2, sH2, a.z2, a.h2, row0, a.rows);
         __syncthreads();
-        if (warp < 4) {   // output layer: m-tile warp/2, n-tile warp%2
+        {   // output layer: m-tile warp/2, n-tile warp%2
             const int mt = warp >> 1, nt = warp & 1;
             float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
             const int q = lane >> 3, r8 = lane & 7;
 #pragma unroll 4
             for (int kk = 0; kk < kMlpH; kk += 16) {
                 uint32_t av[4], b0, b1;
-                ldsm_x4(smem_addr(sH2 + (mt * 16 + (q & 1) * 8 + r8) * kLdH + kk + (q >> 1) * 8), av[0], av[1],
+                ldsm_x4(smem_addr(sH2 + swz256(mt * 16 + (q & 1) * 8 + r8, kk + (q >> 1) * 8)), av[0], av[1],
                         av[2], av[3]);
-                ldsm_x2(smem_addr(sW3 + (nt * 8 + r8) * kLdH + kk + (q & 1) * 8), b0, b1);
+                ldsm_x2(smem_addr(sW3 + swz256(nt * 8 + r8, kk + (q & 1) * 8)), b0, b1);
                 mma_16816(acc, av, b0, b1);
             }
             const int g = lane >> 2, tq = lane & 3;
@@ -178,7 +195,9 @@ __global__ void __launch_bounds__(256, 1) mlp_forward_kernel(const __grid_consta
                     const float ov = acc[2 * hh + cc] + sb3[c];
                     if (a.o) a.o[gr * kMlpOutP + c] = ov;
                     if (a.xout && c < a.d) {
-                        const float disp = fmaf(ov, sd_out[c], mu_out[c]);
+                        // a displacement beyond 8 standard deviations of the
+                        // training targets is not trusted: clamp it there
+                        const float disp = fmaf(fminf(fmaxf(ov, -8.0f), 8.0f), sd_out[c], mu_out[c]);
                         a.xout[gr * a.d + c] = a.u ? a.u[gr * a.d + c] + disp : disp;
                     }
                 }
@@ -398,7 +417,7 @@ __global__ void proposal_rows_kernel(const __grid_constant__ ProposalRowsArgs a)
             if (t > a.Tend[b] || i >= a.Nseq[b]) continue;
             row = a.row_base[(size_t)b * a.maxT + (t - 1)] + i;
         } else {
-            b = (int)(e / a.Nmax);
+            b = a.b_base + (int)(e / a.Nmax);
             i = (int)(e % a.Nmax);
             if (a.tcur[b] >= a.Tend[b] || i >= a.Nseq[b]) continue;
             t = a.tcur[b] + 1;
@@ -445,9 +464,9 @@ const void* proposal_rows_fn(int kind) {
 
 int proposal_in_dim(int kind, int d, int dy) {
     switch (kind) {
-    case 4: return d + 4;
-    case 3: return 2 + 2 * std::min(dy / 2, (kMlpInP - 2) / 2);
-    default: return d + 2 * std::min(dy, (kMlpInP - d) / 2);
+    case 4: return d + 4 + d / 2;
+    case 3: return 4 + 2 * std::min(dy / 2, (kMlpInP - 4) / 2);
+    default: return 2 * d + 2 * std::min(dy, (kMlpInP - 2 * d) / 2);
     }
 }
 
@@ -544,7 +563,7 @@ smap_status launch_forward(smap_proposal* p, const float* feat, const int* idx, 
     a.xout = xout;
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-    const long tiles = (rows + kMlpRows - 1) / kMlpRows;
+    const long tiles = (rows + kFwdRows - 1) / kFwdRows;
     const int grid = (int)std::max<long>(1, std::min<long>(tiles, sms));
     mlp_forward_kernel<<<grid, 256, mlp_fwd_smem(), st>>>(a);
     PCUDA(p, cudaGetLastError());

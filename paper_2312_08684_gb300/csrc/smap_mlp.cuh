@@ -73,16 +73,20 @@ __device__ __forceinline__ void mma_16816(float* d, const uint32_t* a, uint32_t 
 }
 
 // ---------------------------------------------------------------------------
-// Proposal features of a propagated particle u and the observation z.
-//   planar arm : [u (14), z (2), z - h(u) (2)]                       18
+// Proposal features of a propagated particle u and the observation z; each
+// ends with the likelihood score grad_u log p(z | u) (the direction SVGD's
+// drive starts from).
+//   planar arm : [u (14), z (2), z - h(u) (2), score of the angles (7)]   25
 //   clutter    : [velocity (2), z_m - position for the 10 points sorted
-//                 by distance to the position (20)]                  22
-//   others     : [u (d), z (dy) with unheard entries 0, heard flags]
+//                 by distance to the position (20), score of the position (2)] 24
+//   others     : [u (d), z (dy) with unheard entries 0, heard flags, score (d)]
 // Returns the number of features written (<= kMlpInP).
 // ---------------------------------------------------------------------------
 template <class M>
 __device__ int proposal_features(const ModelParams& mp, const float* u, const float* z, float* f) {
     constexpr int D = M::D;
+    float g[D];
+    M::grad_loglik(mp, z, u, g);
     if constexpr (M::KIND == 4) {
         constexpr int NL = D / 2;
         const float* len = mp.pf + 3 + 2 * NL;
@@ -101,7 +105,9 @@ __device__ int proposal_features(const ModelParams& mp, const float* u, const fl
         f[D + 1] = z[1];
         f[D + 2] = z[0] - ex;
         f[D + 3] = z[1] - ey;
-        return D + 4;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) f[D + 4 + l] = g[l];
+        return D + 4 + NL;
     } else if constexpr (M::KIND == 3) {
         const int Mz = (int)mp.p[6];
         f[0] = u[2];
@@ -120,22 +126,26 @@ __device__ int proposal_features(const ModelParams& mp, const float* u, const fl
             while (k >= 0 && dist[ord[k]] > v) { ord[k + 1] = ord[k]; --k; }
             ord[k + 1] = o;
         }
-        const int nm = Mz < (kMlpInP - 2) / 2 ? Mz : (kMlpInP - 2) / 2;
+        const int nm = Mz < (kMlpInP - 4) / 2 ? Mz : (kMlpInP - 4) / 2;
         for (int m = 0; m < nm; ++m) {
             f[2 + 2 * m] = z[2 * ord[m]] - u[0];
             f[3 + 2 * m] = z[2 * ord[m] + 1] - u[1];
         }
-        return 2 + 2 * nm;
+        f[2 + 2 * nm] = g[0];
+        f[3 + 2 * nm] = g[1];
+        return 4 + 2 * nm;
     } else {
         int n = 0;
 #pragma unroll
         for (int c = 0; c < D; ++c) f[n++] = u[c];
-        const int dy = mp.dy < (kMlpInP - D) / 2 ? mp.dy : (kMlpInP - D) / 2;
+        const int dy = mp.dy < (kMlpInP - 2 * D) / 2 ? mp.dy : (kMlpInP - 2 * D) / 2;
         for (int c = 0; c < dy; ++c) {
             const float v = z[c];
             f[n++] = (v == v) ? v : 0.0f;
         }
         for (int c = 0; c < dy; ++c) f[n++] = (z[c] == z[c]) ? 1.0f : 0.0f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) f[n++] = g[c];
         return n;
     }
 }

@@ -161,6 +161,7 @@ extern "C" smap_status smap_viterbi_noalloc(int model, const double* params, int
     a.f64 = c.f64;
     a.bwguess = c.bwguess;
     a.status = c.status;
+    a.stats = c.status + B;
     a.queue = c.queue;
     void* args[] = {&a};
     cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, smem, st);

@@ -146,10 +146,25 @@ def test_capture_rows_match_oracle(oracle, torch):
                     prev = wl.x0[b] if t == 1 else hist[b, t - 2, i].astype(np.float64)
                     u = m.transition(t, prev) + np.sqrt(m.q) * oracle.normals(wl.seed, b, t, i, wl.d)
                     f = oracle.proposal_features(wl.kind, wl.params, u, wl.y[b, t - 1].astype(np.float64))
-                    assert np.allclose(feat[r, :len(f)], f, rtol=1e-5, atol=2e-5)
+                    ns = wl.d // 2          # the arm's score block: the 7 angles
+                    k = len(f) - ns
+                    assert np.allclose(feat[r, :k], f[:k], rtol=1e-5, atol=2e-5)
+                    # the score amplifies FP32 kinematics (fast sincos) by 1/r = 1e4
+                    assert np.allclose(feat[r, k:len(f)], f[k:], rtol=1e-3, atol=1e-4 * max(1.0, np.abs(f[k:]).max()))
                     assert np.all(feat[r, len(f):] == 0)
                     assert np.allclose(targ[r, :wl.d], hist[b, t - 1, i] - u, rtol=1e-4, atol=2e-6)
                     r += 1
+    finally:
+        abi.smap_proposal_destroy(p)
+
+
+def test_untrained_proposal_stays_finite(torch):
+    """Random weights and identity scaling give wild displacements; the
+    clamp at 8 standard deviations keeps the method finite."""
+    wl = W.make_clutter_cv(B=6, Tmin=12, Tmax=12, N=64, L=3)
+    p, _, _ = _prop(torch, wl.kind, wl.params, seed=21)
+    try:
+        assert np.isfinite(_mean_J(wl, 3, p))
     finally:
         abi.smap_proposal_destroy(p)
 

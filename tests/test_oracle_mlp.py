@@ -68,15 +68,18 @@ def test_features_arm_and_clutter(oracle):
     z = rng.normal(0, 1, 2)
     f = oracle.proposal_features(4, p, u, z)
     e = np.sum(0.3 * np.exp(1j * np.cumsum(u[:7])))
-    assert np.allclose(f, np.r_[u, z, z - [e.real, e.imag]], rtol=0, atol=1e-12)
+    g = oracle.Model(4, p).grad_loglik(1, z, u)          # pinned by finite differences
+    assert np.allclose(f, np.r_[u, z, z - [e.real, e.imag], g[:7]], rtol=0, atol=1e-9)
     pc = W.clutter_params()
     u = np.r_[rng.normal(0, 3, 2), rng.normal(0, 1, 2)]
     z = rng.uniform(-10, 10, (10, 2))
     f = oracle.proposal_features(3, pc, u, z.ravel())
     rel = z - u[:2]
     order = np.argsort(np.sum(rel ** 2, 1), kind="stable")
-    assert np.allclose(f, np.r_[u[2:], rel[order].ravel()], rtol=0, atol=1e-12)
+    g = oracle.Model(3, pc).grad_loglik(1, z.ravel(), u)
+    assert np.allclose(f, np.r_[u[2:], rel[order].ravel(), g[:2]], rtol=0, atol=1e-12)
     pr = W.range_params(np.zeros((3, 2)))
     z = np.array([5.0, np.nan, 7.0])
     f = oracle.proposal_features(2, pr, u, z)
-    assert np.allclose(f, np.r_[u, 5.0, 0.0, 7.0, 1.0, 0.0, 1.0])
+    g = oracle.Model(2, pr).grad_loglik(1, z, u)
+    assert np.allclose(f, np.r_[u, 5.0, 0.0, 7.0, 1.0, 0.0, 1.0, g])
