@@ -224,7 +224,9 @@ smap_status smap_proposal_dims(const smap_proposal* p, int* in, int* out, int* h
 /* Host copies of the FP32 parameters / normalisation (either may be NULL). */
 smap_status smap_proposal_get_weights(smap_proposal* p, float* theta, float* norm);
 smap_status smap_proposal_set_weights(smap_proposal* p, const float* theta, const float* norm);
-/* Normalisation from data: column means and standard deviations. */
+/* Normalisation from data: feature column means and standard deviations;
+ * target column means and standard deviations, each standard deviation
+ * floored at 1% of the largest one among the d outputs. */
 smap_status smap_proposal_fit_normalization(smap_proposal* p, const float* feat, const float* targ, long rows);
 /* disp [rows][d] = displacement predicted for feat [rows][32]. Synchronous. */
 smap_status smap_proposal_forward(smap_proposal* p, const float* feat, long rows, float* disp);

@@ -770,10 +770,19 @@ smap_status smap_proposal_fit_normalization(smap_proposal* p, const float* feat,
         norm[c] = (float)mu;
         norm[kMlpInP + c] = (float)(var > 1e-12 ? std::sqrt(var) : 1.0);
     }
+    // Output scales: each target column's spread, floored at 1% of the widest
+    // one, so that coordinates that barely move (noise-level displacements)
+    // do not weigh as much in the loss as the ones that carry the update.
+    double widest = 0.0;
+    for (int c = 0; c < p->d; ++c) {
+        const double mu = h[2 * kMlpInP + c] / rows, var = h[2 * kMlpInP + kMlpOutP + c] / rows - mu * mu;
+        widest = std::max(widest, var > 0.0 ? std::sqrt(var) : 0.0);
+    }
     for (int c = 0; c < kMlpOutP; ++c) {
         const double mu = h[2 * kMlpInP + c] / rows, var = h[2 * kMlpInP + kMlpOutP + c] / rows - mu * mu;
+        const double sd = std::max(var > 0.0 ? std::sqrt(var) : 0.0, 1e-2 * widest);
         norm[2 * kMlpInP + c] = (float)mu;
-        norm[2 * kMlpInP + kMlpOutP + c] = (float)(var > 1e-20 ? std::sqrt(var) : 1.0);
+        norm[2 * kMlpInP + kMlpOutP + c] = (float)(c < p->d && sd > 1e-10 ? sd : 1.0);
     }
     return smap_proposal_set_weights(p, nullptr, norm.data());
 }

@@ -8,7 +8,10 @@ the learned initialisation with a few iterations, on the same GB300.
    particle) into a row (features of the plain initialisation, displacement
    to the final particle).
 2. Training: smap_proposal_train (the library's forward/backward/Adam
-   kernels) on minibatches of those rows.
+   kernels) on minibatches of those rows. With --rounds R > 1, each further
+   round regenerates the training runs with L_plain iterations started from
+   the previous round's network and trains a fresh network on them
+   (self-distillation: the targets are particles after more SVGD progress).
 3. Evaluation on fresh sequences: wall time of smap_run_batch (device-resident
    observations, CUDA events) and the mean MAP log-posterior J for plain
    L_plain, plain L_learned and learned L_learned.
@@ -62,51 +65,66 @@ def main(argv=None):
     ap.add_argument("--N", type=int, default=None)
     ap.add_argument("--T", type=int, default=100)
     ap.add_argument("--train-seqs", type=int, default=1000, help="training sequences (x T steps)")
-    ap.add_argument("--eval-seqs", type=int, default=304)
+    ap.add_argument("--eval-seqs", type=int, default=4096)
     ap.add_argument("--L-plain", type=int, default=50)
     ap.add_argument("--L-learned", type=int, default=5)
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--batch", type=int, default=8192)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--max-rows", type=float, default=1.2e8)
+    ap.add_argument("--rounds", type=int, default=3, help="self-distillation rounds (1 = plain-run data only)")
+    ap.add_argument("--reps", type=int, default=1, help="timed repetitions of each evaluation run")
     args = ap.parse_args(argv)
     import torch
     which = args.workload
     N = args.N or (1024 if which == "arm" else 512)
     t0 = time.time()
-    # 1. training data from plain runs (chunks of sequences)
     probe = _make(which, 1, 2, N, args.L_plain, 0, 100)
-    prop = abi.smap_proposal_create(probe.kind, probe.params, seed=7)
-    n_in, n_out, _, _ = abi.smap_proposal_dims(prop)
     total = min(int(args.max_rows), args.train_seqs * args.T * N)
     feat = torch.empty((total, abi.MLP_IN_P), dtype=torch.float32, device="cuda")
     targ = torch.empty((total, abi.MLP_OUT_P), dtype=torch.float32, device="cuda")
-    rows, done, chunk = 0, 0, 304
-    while done < args.train_seqs and rows < total:
-        b = min(chunk, args.train_seqs - done)
-        wl = _make(which, b, args.T, N, args.L_plain, 100000 + done, 100)
-        with Estimator.from_workload(wl) as est:
-            est.run_batch(wl.y, wl.T)
-            need = wl.B * wl.maxT * N
-            if rows + need > total:
-                break
-            rows += abi.smap_proposal_capture(prop, est.h, feat[rows:], targ[rows:])
-        done += b
-    t_data = time.time() - t0
-    # 2. training
-    abi.smap_proposal_fit_normalization(prop, feat[:rows], targ[:rows])
-    t1 = time.time()
-    curve = abi.smap_proposal_train(prop, feat[:rows], targ[:rows], args.steps, args.batch, args.lr,
-                                    args.lr * 0.05)
-    torch.cuda.synchronize()
-    t_train = time.time() - t1
+    ev = _make(which, args.eval_seqs, args.T, N, args.L_learned, 0, 4)
+    prop, history = None, []
+    for rnd in range(args.rounds):
+        # 1. training data from runs with L_plain iterations (chunks of sequences);
+        #    from the second round on, started from the previous network
+        nxt = abi.smap_proposal_create(probe.kind, probe.params, seed=7 + rnd)
+        rows, done, chunk = 0, 0, 304
+        t0 = time.time()
+        while done < args.train_seqs and rows < total:
+            b = min(chunk, args.train_seqs - done)
+            wl = _make(which, b, args.T, N, args.L_plain, 100000 + done, 100)
+            with Estimator.from_workload(wl) as est:
+                if prop is not None:
+                    abi.smap_set_proposal(est.h, prop, args.L_plain)
+                est.run_batch(wl.y, wl.T)
+                need = wl.B * wl.maxT * N
+                if rows + need > total:
+                    break
+                rows += abi.smap_proposal_capture(nxt, est.h, feat[rows:], targ[rows:])
+            done += b
+        t_data = time.time() - t0
+        # 2. training
+        abi.smap_proposal_fit_normalization(nxt, feat[:rows], targ[:rows])
+        t1 = time.time()
+        curve = abi.smap_proposal_train(nxt, feat[:rows], targ[:rows], args.steps, args.batch, args.lr,
+                                        args.lr * 0.05)
+        torch.cuda.synchronize()
+        t_train = time.time() - t1
+        if prop is not None:
+            abi.smap_proposal_destroy(prop)
+        prop = nxt
+        history.append({"rows": rows, "sequence_steps": done * args.T, "steps": args.steps, "batch": args.batch,
+                        "loss_first": float(np.mean(curve[:20])), "loss_last": float(np.mean(curve[-50:])),
+                        "data_seconds": t_data, "train_seconds": t_train})
+        if args.rounds > 1:
+            history[-1]["learned_mean_J"] = float(np.mean(_run(torch, ev, args.L_learned, prop, reps=1)[1]))
     del feat, targ
     torch.cuda.empty_cache()
     # 3. evaluation on fresh sequences
-    ev = _make(which, args.eval_seqs, args.T, N, args.L_learned, 0, 4)
-    t_plain, J_plain = _run(torch, ev, args.L_plain)
-    t_small, J_small = _run(torch, ev, args.L_learned)
-    t_learn, J_learn = _run(torch, ev, args.L_learned, prop)
+    t_plain, J_plain = _run(torch, ev, args.L_plain, reps=args.reps)
+    t_small, J_small = _run(torch, ev, args.L_learned, reps=args.reps)
+    t_learn, J_learn = _run(torch, ev, args.L_learned, prop, reps=args.reps)
     abi.smap_proposal_destroy(prop)
     mp, ml, ms = float(np.mean(J_plain)), float(np.mean(J_learn)), float(np.mean(J_small))
     out = {
@@ -118,9 +136,7 @@ def main(argv=None):
         "speedup_learned_vs_plain": t_plain / t_learn,
         "J_gap_rel": (mp - ml) / abs(mp),
         "J_gap_rel_without_network": (mp - ms) / abs(mp),
-        "training": {"rows": rows, "sequence_steps": done * args.T, "steps": args.steps, "batch": args.batch,
-                     "loss_first": float(np.mean(curve[:20])), "loss_last": float(np.mean(curve[-50:])),
-                     "data_seconds": t_data, "train_seconds": t_train},
+        "training": history,
     }
     print(json.dumps(out), flush=True)
     return out
