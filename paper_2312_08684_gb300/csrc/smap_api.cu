@@ -387,9 +387,11 @@ cudaMemcpyKind kind_out(int on_device) { return on_device ? cudaMemcpyDeviceToDe
 
 // Reads the per-sequence status words; returns the first failure or OK.
 smap_status collect_status(smap_handle* h) {
-    std::vector<int> st(h->B);
-    SMAP_CUDA(h, cudaMemcpyAsync(st.data(), h->status, sizeof(int) * h->B, cudaMemcpyDeviceToHost, h->stream));
+    std::vector<int> st(h->B + kStatusExtra);
+    SMAP_CUDA(h, cudaMemcpyAsync(st.data(), h->status, sizeof(int) * st.size(), cudaMemcpyDeviceToHost, h->stream));
     SMAP_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (st[h->B + 3] != 0)
+        return fail(h, SMAP_E_CUDA, "learned proposal: the tensor-core network kernel gave up a wait");
     for (int b = 0; b < h->B; ++b) {
         if (st[b] == SMAP_E_NONFINITE)
             return fail(h, SMAP_E_NONFINITE, "sequence " + std::to_string(b) + ": particles or scores became non-finite");
@@ -463,6 +465,7 @@ smap_status batch_device_work(smap_handle* h, int v) {
             ra.x0 = h->x0; ra.hist = h->hist; ra.y = h->y;
             ra.tcur = h->tcur; ra.Tend = h->Tend; ra.Nseq = h->Nseq;
             ra.feat = h->lfeat + r0 * 32; ra.u = h->lu + r0 * h->d;
+            ra.err = h->status + h->B + 3;
             StepOpts so;
             so.xinit = h->lxinit;
             so.y_full = 1;

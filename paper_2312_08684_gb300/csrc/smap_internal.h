@@ -49,6 +49,7 @@ struct ProposalRowsArgs {
     float* feat;                  // [rows][32]
     float* u;                     // [rows][d] or null
     float* targ;                  // [rows][16] or null (capture)
+    int* err;                     // learned initialisation: set to 1 if the network kernel gave up a wait
 };
 
 // Defined in smap_mlp.cu.

@@ -485,6 +485,7 @@ struct smap_proposal {
     float *theta = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *norm = nullptr;
     bf16 *W1b = nullptr, *W2b = nullptr, *W3b = nullptr;
     double* lossd = nullptr;
+    int* tcerr = nullptr;         // error word of the tensor-core forward
     // training scratch (capacity R_cap rows)
     long R_cap = 0;
     int* idx = nullptr;
@@ -539,8 +540,36 @@ smap_status ensure_scratch(smap_proposal* p, long R) {
 
 int grid_for(long n, int block) { return (int)std::min<long>((n + block - 1) / block, 152L * 16); }
 
+int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+    }
+    return sms;
+}
+
+// Inference (no training outputs, no gather) runs on the tcgen05 kernel;
+// training passes keep the mma.sync kernel, which also writes the layer
+// activations that the backward pass reads.
 smap_status launch_forward(smap_proposal* p, const float* feat, const int* idx, long rows, bool train,
-                           const float* u, float* xout, cudaStream_t st) {
+                           const float* u, float* xout, cudaStream_t st, int* err = nullptr) {
+    if (!train && !idx && xout) {
+        MlpTcArgs t;
+        t.W1 = p->W1b; t.W2 = p->W2b; t.W3 = p->W3b;
+        t.b1 = p->theta + kMlpB1; t.b2 = p->theta + kMlpB2; t.b3 = p->theta + kMlpB3;
+        t.norm = p->norm;
+        t.rows = rows;
+        t.d = p->d;
+        t.feat = feat;
+        t.u = u;
+        t.xout = xout;
+        t.err = err ? err : p->tcerr;
+        PCUDA(p, mlp_forward_tc_launch(t, num_sms(), st));
+        g_launches.fetch_add(1);
+        return SMAP_OK;
+    }
     static bool configured = false;
     if (!configured) {
         PCUDA(p, cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -561,10 +590,8 @@ smap_status launch_forward(smap_proposal* p, const float* feat, const int* idx, 
     }
     a.u = u;
     a.xout = xout;
-    int sms = 152;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
     const long tiles = (rows + kFwdRows - 1) / kFwdRows;
-    const int grid = (int)std::max<long>(1, std::min<long>(tiles, sms));
+    const int grid = (int)std::max<long>(1, std::min<long>(tiles, num_sms()));
     mlp_forward_kernel<<<grid, 256, mlp_fwd_smem(), st>>>(a);
     PCUDA(p, cudaGetLastError());
     g_launches.fetch_add(1);
@@ -629,7 +656,7 @@ smap_status proposal_launch_init(smap_proposal* p, const ProposalRowsArgs& ra, f
     void* args[] = {const_cast<ProposalRowsArgs*>(&ra)};
     PCUDA(p, cudaLaunchKernel(fn, dim3(grid_for(total, 256)), dim3(256), args, 0, st));
     g_launches.fetch_add(1);
-    return launch_forward(p, ra.feat, nullptr, total, false, ra.u, xinit, st);
+    return launch_forward(p, ra.feat, nullptr, total, false, ra.u, xinit, st, ra.err);
 }
 
 smap_status proposal_launch_capture(smap_proposal* p, const ProposalRowsArgs& ra, cudaStream_t st) {
@@ -680,7 +707,7 @@ smap_status smap_proposal_create(int model, const double* params, int n_params, 
         {(void**)&p->v, sizeof(float) * kMlpNP}, {(void**)&p->grad, sizeof(float) * kMlpNP},
         {(void**)&p->norm, sizeof(float) * (2 * kMlpInP + 2 * kMlpOutP)},
         {(void**)&p->W1b, sizeof(bf16) * kMlpH * kMlpInP}, {(void**)&p->W2b, sizeof(bf16) * kMlpH * kMlpH},
-        {(void**)&p->W3b, sizeof(bf16) * kMlpOutP * kMlpH}, {(void**)&p->lossd, sizeof(double) * 4},
+        {(void**)&p->W3b, sizeof(bf16) * kMlpOutP * kMlpH}, {(void**)&p->lossd, sizeof(double) * 4}, {(void**)&p->tcerr, sizeof(int)},
     };
     for (auto& a : al)
         if (cudaMalloc(a.q, a.bytes) != cudaSuccess) {
@@ -688,6 +715,7 @@ smap_status smap_proposal_create(int model, const double* params, int n_params, 
             return bail(SMAP_E_NOMEM);
         }
     cudaMemsetAsync(p->m, 0, sizeof(float) * kMlpNP, p->stream);
+    cudaMemsetAsync(p->tcerr, 0, sizeof(int), p->stream);
     cudaMemsetAsync(p->v, 0, sizeof(float) * kMlpNP, p->stream);
     std::vector<float> norm(2 * kMlpInP + 2 * kMlpOutP, 0.0f);
     for (int c = 0; c < kMlpInP; ++c) norm[kMlpInP + c] = 1.0f;
@@ -705,7 +733,7 @@ void smap_proposal_destroy(smap_proposal* p) {
     if (!p) return;
     if (p->stream) cudaStreamSynchronize(p->stream);
     free_scratch(p);
-    void* bufs[] = {p->theta, p->m, p->v, p->grad, p->norm, p->W1b, p->W2b, p->W3b, p->lossd};
+    void* bufs[] = {p->theta, p->m, p->v, p->grad, p->norm, p->W1b, p->W2b, p->W3b, p->lossd, p->tcerr};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
@@ -791,7 +819,13 @@ smap_status smap_proposal_forward(smap_proposal* p, const float* feat, long rows
     if (!p || !feat || !disp || rows < 1) return SMAP_E_INVAL;
     smap_status s = launch_forward(p, feat, nullptr, rows, false, nullptr, disp, p->stream);
     if (s) return s;
+    int err = 0;
+    PCUDA(p, cudaMemcpyAsync(&err, p->tcerr, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     PCUDA(p, cudaStreamSynchronize(p->stream));
+    if (err) {
+        cudaMemsetAsync(p->tcerr, 0, sizeof(int), p->stream);
+        return pfail(p, SMAP_E_CUDA, "tensor-core forward: a wait gave up (results not written)");
+    }
     return SMAP_OK;
 }
 

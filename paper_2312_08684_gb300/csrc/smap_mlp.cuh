@@ -30,6 +30,22 @@ constexpr long kMlpW3 = kMlpB2 + kMlpH;
 constexpr long kMlpB3 = kMlpW3 + (long)kMlpOutP * kMlpH;
 constexpr long kMlpNP = kMlpB3 + kMlpOutP;
 
+// Inference forward on the 5th-generation tensor cores (smap_mlp_tc.cu):
+// xout[r][c] = u[r][c] (or 0) + sd_out[c] clamp(MLP(standardised feat[r]), +-8)[c] + mu_out[c].
+struct MlpTcArgs {
+    const __nv_bfloat16 *W1, *W2, *W3;   // compact BF16 [H][InP], [H][H], [OutP][H]
+    const float *b1, *b2, *b3;
+    const float* norm;                   // mu_in[InP], sd_in[InP], mu_out[OutP], sd_out[OutP]
+    long rows;
+    int d;                               // real output width
+    const float* feat;                   // [rows][InP]
+    const float* u;                      // [rows][d] or null
+    float* xout;                         // [rows][d]
+    int* err;                            // set to 1 when a wait gave up (may be null)
+};
+size_t mlp_forward_tc_smem();
+cudaError_t mlp_forward_tc_launch(const MlpTcArgs& a, int num_sms, cudaStream_t st);
+
 __device__ __forceinline__ float tanh_approx(float x) {
     float y;
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));

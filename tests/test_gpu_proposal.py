@@ -76,6 +76,35 @@ def test_forward_matches_oracle(oracle, torch):
         abi.smap_proposal_destroy(p)
 
 
+def test_forward_many_tiles_matches_oracle(oracle, torch):
+    """More 128-row tiles than SMs (several per persistent CTA) plus a ragged
+    tail: sampled rows against the oracle, the rest must be finite."""
+    p, n_in, n_out = _prop(torch, 3, W.clutter_params(), seed=4)
+    try:
+        rng = np.random.default_rng(5)
+        theta, norm = abi.smap_proposal_get_weights(p)
+        norm[:n_in] = rng.normal(0, 1, n_in)
+        norm[INP:INP + n_in] = rng.uniform(0.5, 2.0, n_in)
+        norm[2 * INP:2 * INP + n_out] = rng.normal(0, 0.1, n_out)
+        norm[2 * INP + OUTP:2 * INP + OUTP + n_out] = rng.uniform(0.01, 0.1, n_out)
+        abi.smap_proposal_set_weights(p, theta, norm)
+        R = 152 * 128 * 3 + 77
+        feat = np.zeros((R, INP), np.float32)
+        feat[:, :n_in] = rng.normal(0, 2, (R, n_in))
+        disp = torch.full((R, n_out), float("nan"), dtype=torch.float32, device="cuda")
+        abi.smap_proposal_forward(p, torch.from_numpy(feat).cuda(), disp)
+        got = disp.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        rows = np.r_[np.arange(0, R, 41), np.arange(R - 130, R)]
+        xn = bf16((feat[rows, :n_in] - norm[:n_in]) / norm[INP:INP + n_in])
+        o = oracle.mlp_forward(n_in, H, n_out, unpack(theta, n_in, n_out), xn)
+        ref = o * norm[2 * INP + OUTP:2 * INP + OUTP + n_out] + norm[2 * INP:2 * INP + n_out]
+        spread = np.std(ref, axis=0).max()
+        assert np.max(np.abs(got[rows] - ref)) <= 3e-2 * spread
+    finally:
+        abi.smap_proposal_destroy(p)
+
+
 def test_gradient_matches_oracle(oracle, torch):
     p, n_in, n_out = _prop(torch, 3, W.clutter_params())
     try:
