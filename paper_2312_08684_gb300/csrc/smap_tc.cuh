@@ -25,6 +25,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo_bytes,
            ((uint64_t)1 << 46) | (swizzle << 61);
 }
 
+// The descriptor of an operand `bytes` further on (a multiple of 16) in the
+// same region: only the start-address field changes, without carry since
+// shared addresses stay below 256 KB.
+__device__ __forceinline__ uint64_t desc_add(uint64_t desc, uint32_t bytes) { return desc + (uint64_t)(bytes >> 4); }
+
 // Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
 // K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
@@ -100,14 +105,26 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Suspending check: the thread may sleep (a hardware-chosen time) until the
+// phase completes; returns whether it did.
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // Waits for the phase of the given parity to complete; gives up after about
 // `limit_ns` nanoseconds of global time and returns false.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
-    if (mbar_test(bar, parity)) return true;
+    if (mbar_try(bar, parity)) return true;
     uint64_t t0;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
     for (;;) {
-        if (mbar_test(bar, parity)) return true;
+        if (mbar_try(bar, parity)) return true;
         uint64_t t;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
         if (t - t0 > limit_ns) return false;
@@ -121,6 +138,31 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
     const bool ok = mbar_wait(bar, parity, limit_ns);
     return __all_sync(0xffffffffu, ok);
+}
+
+// Warp-uniform bounded wait with little shared-memory traffic: lane 0 polls,
+// sleeping `sleep_ns` between polls; once it saw the phase complete, every
+// lane checks the (completed) phase itself, which gives each lane the
+// barrier's acquire ordering.
+__device__ __forceinline__ bool warp_wait_sleep(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
+                                                unsigned sleep_ns) {
+    uint32_t ok = 1;
+    if ((threadIdx.x & 31) == 0) {
+        if (!mbar_test(bar, parity)) {
+            uint64_t t0;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+            for (;;) {
+                __nanosleep(sleep_ns);
+                if (mbar_test(bar, parity)) break;
+                uint64_t t;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                if (t - t0 > limit_ns) { ok = 0; break; }
+            }
+        }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) return false;
+    return __all_sync(0xffffffffu, mbar_test(bar, parity));
 }
 
 }  // namespace tc
