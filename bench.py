@@ -66,6 +66,26 @@ def algorithmic_ops(wl) -> float:
     return float(np.sum(n2 * T * (wl.L * (8 * d + 8) + (4 * d + 4))))
 
 
+def seq_kernel_traffic(wl):
+    """DRAM bytes (read + write) of one step-kernel launch on this workload,
+    from the committed ncu summary of the same command; None when there is no
+    summary for this exact configuration."""
+    path = os.path.join(ROOT, "profiles", "seq_kernel_range_cv_traffic.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("traffic:"):
+                for kv in line[len("traffic:"):].split():
+                    k, v = kv.split("=")
+                    vals[k] = int(v)
+    want = (wl.B, wl.maxT, wl.N, wl.L)
+    if (vals.get("B"), vals.get("T"), vals.get("N"), vals.get("L")) != want:
+        return None
+    return vals.get("bytes_per_launch")
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -276,11 +296,7 @@ def main():
     peak = alu_peak_gops(sm_for_peak)
     kms = float(np.mean(kern_ms))
     achieved = algorithmic_ops(wl) / (kms / 1000.0) / 1e9
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_path):
-        with open(tr_path) as f:
-            traffic = json.load(f).get("seq_kernel_bytes_per_launch")
+    traffic = seq_kernel_traffic(wl)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
