@@ -2,6 +2,7 @@
 the learned initialisation with a few iterations, on the same GB300.
 
   python -m paper_2312_08684_gb300.learned --workload arm|clutter [options]
+  python -m paper_2312_08684_gb300.learned --forward-only ROWS [--reps K]
 
 1. Training data: plain runs (L_plain iterations) of sequences disjoint from
    the evaluation set; smap_proposal_capture turns every (sequence, step,
@@ -59,6 +60,34 @@ def _run(torch, wl, L, prop=None, reps=2):
     return float(np.min(times)), Jh
 
 
+def forward_only(rows, reps):
+    """Times the inference forward (the tensor-core kernel) alone on `rows`
+    random standardised feature rows of the clutter network shape."""
+    import torch
+    probe = _make("clutter", 1, 2, 512, 5, 0, 100)
+    p = abi.smap_proposal_create(probe.kind, probe.params, seed=3)
+    n_in, n_out, _, _ = abi.smap_proposal_dims(p)
+    g = torch.Generator(device="cuda").manual_seed(1)
+    feat = torch.zeros((rows, abi.MLP_IN_P), dtype=torch.float32, device="cuda")
+    feat[:, :n_in] = torch.randn((rows, n_in), device="cuda", generator=g)
+    disp = torch.empty((rows, n_out), dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        abi.smap_proposal_forward(p, feat, disp)
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        abi.smap_proposal_forward(p, feat, disp)   # synchronous
+        ts.append(time.perf_counter() - t0)
+    abi.smap_proposal_destroy(p)
+    t = float(np.median(ts))
+    flop = 2.0 * rows * (abi.MLP_IN_P * abi.MLP_H + abi.MLP_H * abi.MLP_H + abi.MLP_H * abi.MLP_OUT_P)
+    out = {"forward_rows": rows, "ms": t * 1e3, "tflops_padded": flop / t / 1e12,
+           "timing": "host wall clock around the synchronous call, median of reps",
+           "finite": bool(torch.isfinite(disp).all())}
+    print(json.dumps(out), flush=True)
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="arm", choices=["arm", "clutter"])
@@ -74,7 +103,11 @@ def main(argv=None):
     ap.add_argument("--max-rows", type=float, default=1.2e8)
     ap.add_argument("--rounds", type=int, default=3, help="self-distillation rounds (1 = plain-run data only)")
     ap.add_argument("--reps", type=int, default=1, help="timed repetitions of each evaluation run")
+    ap.add_argument("--forward-only", type=int, default=0, metavar="ROWS",
+                    help="only time the network's inference forward on ROWS rows")
     args = ap.parse_args(argv)
+    if args.forward_only:
+        return forward_only(args.forward_only, max(args.reps, 1))
     import torch
     which = args.workload
     N = args.N or (1024 if which == "arm" else 512)
