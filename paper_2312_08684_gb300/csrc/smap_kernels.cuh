@@ -125,11 +125,13 @@ __device__ __forceinline__ float sqdist(const float* a, const float* b) {
 // a3: exact median of the N(N-1)/2 squared distances.
 // ---------------------------------------------------------------------------
 
-// Visits every unordered pair (i < k) once. Unit u pairs row u with row N-1-u,
-// so every unit has N-1 pairs; a unit is split over S threads when the block
-// has more threads than units.
+// Visits every unordered pair (i < k) once, as f(d_ik) with the squared
+// distance d_ik = |x_i|^2 + |x_k|^2 - 2 x_i . x_k from the norms in nrm,
+// clamped at 0 (so the keys order as unsigned integers). Unit u pairs row u
+// with row N-1-u, so every unit has N-1 pairs; a unit is split over S threads
+// when the block has more threads than units.
 template <int D, int DP, class F>
-__device__ __forceinline__ void for_each_pair(const float* xs, int N, F& f) {
+__device__ __forceinline__ void for_each_pair(const float* xs, const float* nrm, int N, F& f) {
     if (N < 2) return;
     const int units = (N + 1) >> 1;
     const int NT = blockDim.x;
@@ -145,28 +147,43 @@ __device__ __forceinline__ void for_each_pair(const float* xs, int N, F& f) {
         if (m0 < e1) {
             float xr[D];
             load_row<D, DP>(xs, r, xr);
+            const float nr = nrm[r];
+#pragma unroll
+            for (int c = 0; c < D; ++c) xr[c] *= -2.0f;
 #pragma unroll 4
             for (int m = m0; m < e1; ++m) {
                 float xk[D];
                 load_row<D, DP>(xs, r + 1 + m, xk);
-                f(sqdist<D>(xr, xk));
+                float v = nr + nrm[r + 1 + m];
+#pragma unroll
+                for (int c = 0; c < D; ++c) v = fmaf(xr[c], xk[c], v);
+                f(fmaxf(v, 0.0f));
             }
         }
         const int b2 = max(m0, len1);
         if (b2 < m1) {
             float xr[D];
             load_row<D, DP>(xs, r2, xr);
+            const float nr = nrm[r2];
+#pragma unroll
+            for (int c = 0; c < D; ++c) xr[c] *= -2.0f;
 #pragma unroll 4
             for (int m = b2; m < m1; ++m) {
+                const int k = r2 + 1 + (m - len1);
                 float xk[D];
-                load_row<D, DP>(xs, r2 + 1 + (m - len1), xk);
-                f(sqdist<D>(xr, xk));
+                load_row<D, DP>(xs, k, xk);
+                float v = nr + nrm[k];
+#pragma unroll
+                for (int c = 0; c < D; ++c) v = fmaf(xr[c], xk[c], v);
+                f(fmaxf(v, 0.0f));
             }
         }
     }
 }
 
-// Counts keys below lo and collects the keys in [lo, hi].
+// Counts keys below lo and collects the keys in [lo, hi]. A bracket holds a
+// few hundred of the N(N-1)/2 keys, so the collection is a rarely taken branch
+// with a plain shared atomic (cheaper per pair than a warp vote).
 struct BracketCount {
     float lo, hi;
     int nlo;
@@ -174,18 +191,9 @@ struct BracketCount {
     int* ncand;
     __device__ __forceinline__ void operator()(float v) {
         nlo += v < lo;
-        const bool in = (v >= lo) & (v <= hi);
-        const unsigned act = __activemask();
-        const unsigned bal = __ballot_sync(act, in);
-        if (bal) {
-            const int leader = __ffs(act) - 1;
-            int base = 0;
-            if ((int)lane_id() == leader) base = atomicAdd(ncand, __popc(bal));
-            base = __shfl_sync(act, base, leader);
-            if (in) {
-                const int idx = base + __popc(bal & ((1u << lane_id()) - 1u));
-                if (idx < kCandCap) cand[idx] = __float_as_uint(v);
-            }
+        if (v >= lo && v <= hi) {
+            const int idx = atomicAdd(ncand, 1);
+            if (idx < kCandCap) cand[idx] = __float_as_uint(v);
         }
     }
 };
@@ -229,7 +237,7 @@ __device__ uint32_t radix_select(const Sm& s, int N, int rank) {
         for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
         __syncthreads();
         RadixHist f{prefix, mask, shift, hist};
-        for_each_pair<D, DP>(s.xs, N, f);
+        for_each_pair<D, DP>(s.xs, s.nrm, N, f);
         __syncthreads();
         if (threadIdx.x == 0) {
             int cum = 0, bsel = 255;
@@ -274,7 +282,7 @@ __device__ bool bracket_pass(const Sm& s, int N, float lo, float hi, int r1, int
     if (threadIdx.x == 0) *s.ncand = 0;
     __syncthreads();
     BracketCount f{lo, hi, 0, s.cand, s.ncand};
-    for_each_pair<D, DP>(s.xs, N, f);
+    for_each_pair<D, DP>(s.xs, s.nrm, N, f);
     const int nlo = block_sum_int(f.nlo, s.redi);   // ends with a barrier
     const int nc = *s.ncand;
     nc_out = nc;
@@ -329,7 +337,7 @@ __device__ bool locate_pass(const Sm& s, int N, uint32_t key_lo, int shift, int 
     for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     KeyHist f{key_lo, shift, hist};
-    for_each_pair<D, DP>(s.xs, N, f);
+    for_each_pair<D, DP>(s.xs, s.nrm, N, f);
     __syncthreads();
     if (threadIdx.x == 0) {
         int cum = 0, b1 = -1, b2 = -1, c1 = 0, cnt = 0;
@@ -386,6 +394,16 @@ __device__ float median_sqdist(const Sm& s, int N, float s2, float q_extra, MedS
     const int r1 = (P & 1) ? (P - 1) / 2 : P / 2 - 1;
     const int r2 = (P & 1) ? r1 : P / 2;
     const int target = 128;   // candidates a bracket aims at
+    // norms of the (scaled) particles for the pair distances; nrm is free here
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        float xi[D];
+        load_row<D, DP>(s.xs, i, xi);
+        float n = 0.0f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) n = fmaf(xi[c], xi[c], n);
+        s.nrm[i] = n;
+    }
+    __syncthreads();
     uint32_t v1 = 0, v2 = 0;
     int nc = 0, path = 2;
     float width = 0.0f;       // key-value width of the bracket that succeeded
