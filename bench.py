@@ -59,11 +59,21 @@ def make_workload(rank: int, B: int, T: int, N: int, L: int):
 def algorithmic_ops(wl) -> float:
     """FP32/SFU lane operations the method needs (per ordered pair-iteration
     8d+8: RBF kernel and update 4d+1 + exp, mixture prior 3d+4 + exp, median
-    d+1; per ordered pair-step of the recursion screen 4d+4)."""
+    d+1; per ordered pair-step of the recursion 2d+2: d differences, d
+    weighted squares, one add of the previous score, one comparison)."""
     d = wl.d
     n2 = wl.Nseq.astype(np.float64) ** 2
     T = wl.T.astype(np.float64)
-    return float(np.sum(n2 * T * (wl.L * (8 * d + 8) + (4 * d + 4))))
+    return float(np.sum(n2 * T * (wl.L * (8 * d + 8) + (2 * d + 2))))
+
+
+def recursion_ops(wl) -> float:
+    """Lane operations of the Viterbi recursion alone (2d+2 per ordered pair
+    of consecutive particle sets; the first step has one predecessor)."""
+    d = wl.d
+    n = wl.Nseq.astype(np.float64)
+    T = wl.T.astype(np.float64)
+    return float(np.sum((n * n * (T - 1) + n) * (2 * d + 2)))
 
 
 def seq_kernel_traffic(wl):
@@ -285,6 +295,24 @@ def main():
             e2e_t.append(time.perf_counter() - t0)
     e2e_s = max_over_ranks(float(np.mean(e2e_t)), dist, f"cuda:{local}")
 
+    # the recursion alone (smap_viterbi on this run's particle sets): its own
+    # roofline against the same ALU peak
+    hist_dev = torch.empty((wl.B, wl.maxT, wl.N, wl.d), dtype=torch.float32, device=f"cuda:{local}")
+    abi.smap_get_history(est.h, hist_dev)
+    abi.smap_viterbi(est.h, hist_dev, y_dev, None, None, path_dev, J_dev)
+    vit_ms = []
+    for _ in range(3):
+        flush.zero_()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            abi.smap_viterbi(est.h, hist_dev, y_dev, None, None, path_dev, J_dev)
+            ev1.record(stream)
+        ev1.synchronize()
+        vit_ms.append(ev0.elapsed_time(ev1))
+    vit_ms = max_over_ranks(float(np.mean(vit_ms)), dist, f"cuda:{local}")
+    del hist_dev
+
     if rank != 0:
         est.close()
         if dist:
@@ -314,6 +342,10 @@ def main():
         "e2e": {"value": units_rank * world / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(wl.y.nbytes),
                 "d2h_bytes_per_step": int(path_pin.numel() * 4 + J_pin.numel() * 8)},
+        "viterbi": {"what": "smap_viterbi alone on the same particle sets (history copy, recursion, "
+                            "backtrack)", "ms": vit_ms,
+                    "achieved": recursion_ops(wl) / (vit_ms / 1000.0) / 1e9, "peak": peak, "unit": "Gop/s",
+                    "frac": recursion_ops(wl) / (vit_ms / 1000.0) / 1e9 / peak, "ops_per_pair": 2 * wl.d + 2},
         "gpu_launches": int(launches),
         "clocks": clk,
     }

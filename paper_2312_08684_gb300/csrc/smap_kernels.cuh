@@ -858,37 +858,69 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
         Lmax[p] = -INFINITY;
     }
     const float cl = -(0.5f + Ku) * kLam, cu = -(0.5f - Ku) * kLam;
-    // pass 1: the best guaranteed lower bound
+    // One FP32 pass: per particle the best lower bound L1 (first j attaining
+    // it), that j's upper bound U1, and the largest upper bound Uo of every
+    // other j. Uo < L1 proves j1 the unique FP64 maximum, so each lane then
+    // evaluates one FP64 score, all lanes together (no divergent FP64 work).
+    float L1[PPT], U1[PPT], Uo[PPT];
+    int j1[PPT];
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        L1[p] = -INFINITY;
+        U1[p] = -INFINITY;
+        Uo[p] = -INFINITY;
+        j1[p] = 0;
+    }
     for (int j = 0; j < Np; ++j) {
         float fj[D];
         load_row<D, DP>(s.fs, j, fj);
-        const float am = ab[j].y;
+        const float2 abj = ab[j];
 #pragma unroll
-        for (int p = 0; p < PPT; ++p)
-            Lmax[p] = fmaxf(Lmax[p], fmaf(cl, sqdist<D>(xc[p], fj), am - C[p]));
+        for (int p = 0; p < PPT; ++p) {
+            const float dist = sqdist<D>(xc[p], fj);
+            const float L = fmaf(cl, dist, abj.y - C[p]);
+            const float U = fmaf(cu, dist, abj.x + C[p]);
+            const bool nb = L > L1[p];
+            Uo[p] = fmaxf(Uo[p], nb ? U1[p] : U);
+            U1[p] = nb ? U : U1[p];
+            L1[p] = nb ? L : L1[p];
+            j1[p] = nb ? j : j1[p];
+        }
     }
-    // pass 2: FP64 evaluation of every candidate whose upper bound reaches Lmax
-    // (the FP32 particle is re-read from shared memory: candidates are rare)
     double bs[PPT], blt[PPT];
     int row[PPT];
+    bool multi = false;
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         row[p] = min(tid + p * NT, N - 1) * DP;
         bs[p] = -INFINITY;
         blt[p] = 0.0;
         best[p] = 0;
+        if (Uo[p] < L1[p]) {
+            const int j = j1[p];
+            blt[p] = mp.logtrans_c - 0.5 * trans_m64<D>(mp, s.xs + row[p], f64 + (size_t)j * D);
+            bs[p] = s.phis[j] + blt[p];
+            best[p] = j;
+        } else {
+            multi = true;
+        }
     }
-    for (int j = 0; j < Np; ++j) {
-        float fj[D];
-        load_row<D, DP>(s.fs, j, fj);
-        const float ap = ab[j].x;
+    if (multi) {
+        // near-ties (rare): every j whose upper bound reaches L1, in FP64,
+        // lowest j first
+        for (int j = 0; j < Np; ++j) {
+            float fj[D];
+            load_row<D, DP>(s.fs, j, fj);
+            const float ap = ab[j].x;
 #pragma unroll
-        for (int p = 0; p < PPT; ++p) {
-            const float U = fmaf(cu, sqdist<D>(xc[p], fj), ap + C[p]);
-            if (U >= Lmax[p]) {
-                const double lt = mp.logtrans_c - 0.5 * trans_m64<D>(mp, s.xs + row[p], f64 + (size_t)j * D);
-                const double sv = s.phis[j] + lt;
-                if (sv > bs[p]) { bs[p] = sv; blt[p] = lt; best[p] = j; }
+            for (int p = 0; p < PPT; ++p) {
+                if (Uo[p] < L1[p]) continue;
+                const float U = fmaf(cu, sqdist<D>(xc[p], fj), ap + C[p]);
+                if (U >= L1[p]) {
+                    const double lt = mp.logtrans_c - 0.5 * trans_m64<D>(mp, s.xs + row[p], f64 + (size_t)j * D);
+                    const double sv = s.phis[j] + lt;
+                    if (sv > bs[p]) { bs[p] = sv; blt[p] = lt; best[p] = j; }
+                }
             }
         }
     }
