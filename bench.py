@@ -161,7 +161,7 @@ def cpu_baseline(wl_full, threads: int, T_sample: int):
     """The FP64 oracle as it stands, one sequence per host thread, T_sample steps."""
     from oracle import oracle as O
     O.lib()
-    nseq = threads
+    nseq = min(threads, wl_full.B)
     sub = wl_full.subset(np.arange(nseq))
     T = np.full(nseq, T_sample, np.int32)
     t0 = time.perf_counter()
@@ -170,9 +170,72 @@ def cpu_baseline(wl_full, threads: int, T_sample: int):
                 nthreads=threads)
     dt = time.perf_counter() - t0
     units = nseq * sub.N * sub.L * T_sample
-    return {"value": units / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+    return {"value": units / dt, "unit": UNIT, "cores": nseq, "kind": "oracle",
             "sample": f"{nseq} sequences x first {T_sample} of {wl_full.maxT} steps "
                       f"(N={sub.N}, L={sub.L}), one sequence per host thread, {dt:.1f} s"}
+
+
+CONFIGS = {
+    # name: (workload builder, oracle sample steps); the shapes of the paper's scenarios
+    "C1 ngm1d": (lambda: W.make_ngm1d(), 50),
+    "C2 range_cv": (lambda: W.make_range_cv(), 6),
+    "C3 clutter_cv": (lambda: W.make_clutter_cv(), 6),
+    "C4 planar_arm": (lambda: W.make_planar_arm(), 1),
+}
+
+
+def all_configs(args):
+    """One JSON line per configuration (one GPU): batched run of the whole
+    configuration timed with CUDA events (inputs resident), the step kernel's
+    ALU roofline, the recursion alone, and the oracle on a bounded sample."""
+    import torch
+    from paper_2312_08684_gb300 import Estimator, _binding as abi
+    pk, src = peaks()
+    sm_for_peak = pk.get("sm_max_mhz", 2070.0)
+    peak = alu_peak_gops(sm_for_peak)
+    for name, (mk, t_sample) in CONFIGS.items():
+        wl = mk()
+        stream = torch.cuda.Stream()
+        y = torch.from_numpy(wl.y).cuda()
+        path = torch.empty((wl.B, wl.maxT + 1, wl.d), dtype=torch.float32, device="cuda")
+        J = torch.empty(wl.B, dtype=torch.float64, device="cuda")
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with Estimator.from_workload(wl, stream=stream) as est:
+            def timed(fn, reps):
+                ms, kms = [], []
+                for _ in range(reps):
+                    torch.cuda.synchronize()
+                    with torch.cuda.stream(stream):
+                        ev0.record(stream)
+                        fn()
+                        ev1.record(stream)
+                    ev1.synchronize()
+                    ms.append(ev0.elapsed_time(ev1))
+                return float(np.mean(ms))
+            run = lambda: abi.smap_run_batch(est.h, y, wl.T, wl.Nseq, path, J)
+            for _ in range(max(args.warmup, 3)):
+                run()
+            ms = timed(run, args.steps)
+            kms = abi.smap_last_kernel_ms(est.h)[0]
+            hist = torch.empty((wl.B, wl.maxT, wl.N, wl.d), dtype=torch.float32, device="cuda")
+            abi.smap_get_history(est.h, hist)
+            vit = lambda: abi.smap_viterbi(est.h, hist, y, wl.T, wl.Nseq, path, J)
+            vit()
+            vms = timed(vit, 3)
+            del hist
+        units = wl.particle_updates()
+        ach = algorithmic_ops(wl) / (kms / 1000.0) / 1e9
+        vach = recursion_ops(wl) / (vms / 1000.0) / 1e9
+        line = {"config": name, "B": wl.B, "N": wl.N, "d": wl.d, "L": wl.L,
+                "T": f"{int(wl.T.min())}..{int(wl.T.max())}" if wl.T.min() != wl.T.max() else int(wl.T[0]),
+                "metric": METRIC, "value": units / (ms / 1000.0), "unit": UNIT, "ms_per_batch": ms,
+                "sequences_per_s": wl.B / (ms / 1000.0),
+                "roofline": {"bound": "alu", "kernel": "seq_kernel", "kernel_ms": kms, "achieved": ach,
+                             "peak": peak, "unit": "Gop/s", "frac": ach / peak},
+                "viterbi": {"ms": vms, "achieved": vach, "frac": vach / peak, "unit": "Gop/s"},
+                "cpu_baseline": cpu_baseline(wl, os.cpu_count() or 1, min(t_sample, int(wl.T.min())))}
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -225,9 +288,13 @@ def main():
     ap.add_argument("--L", type=int, default=WORKLOAD["L"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--all-configs", action="store_true",
+                    help="one line per workload configuration (C1-C4) instead of the bench line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.all_configs:
+        return all_configs(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
