@@ -43,7 +43,10 @@ class _RunCfg(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("params", _D), ("np", ctypes.c_int),
                 ("N", ctypes.c_int), ("L", ctypes.c_int), ("eps", ctypes.c_double),
                 ("bw_rule", ctypes.c_int), ("bw_value", ctypes.c_double),
-                ("prior", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("prior", ctypes.c_int), ("seed", ctypes.c_uint64), ("kernel", ctypes.c_int)]
+
+# Stein kernels of the oracle (om_kernel): 0 RBF, 1 IMQ, 2 Matern 3/2
+KERNEL_RBF, KERNEL_IMQ, KERNEL_MATERN32 = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -82,10 +85,11 @@ def lib():
             L.om_bandwidth.restype = ctypes.c_double
             L.om_grad_prior.argtypes = [P, ctypes.c_int, _D, ctypes.c_int, _D, _D]
             L.om_svgd_iteration.argtypes = [P, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_int,
-                                            _D, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+                                            _D, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_int]
             L.om_svgd_iters.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                         _D, _D, ctypes.c_int, _D, ctypes.c_int, ctypes.c_int,
-                                        ctypes.c_double, _D]
+                                        ctypes.c_double, _D, ctypes.c_int]
             L.om_forward.argtypes = [P, ctypes.c_int, _D, _D, ctypes.c_int, _D, _D, ctypes.c_int,
                                      _I, _D]
             L.om_backtrack.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _I, _D,
@@ -110,7 +114,7 @@ def lib():
             L.om_run_batch.argtypes = [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                        ctypes.c_uint64, ctypes.c_int, _I, _D, ctypes.c_int, _I, _D,
-                                       _D, _D, ctypes.c_int]
+                                       _D, _D, ctypes.c_int, ctypes.c_int]
             _lib = L
     return _lib
 
@@ -168,18 +172,19 @@ class Model:
         lib().om_grad_prior(self.ref, int(prior), _dp(fprev), fprev.shape[0], _dp(x), _dp(g))
         return g
 
-    def svgd_iteration(self, prior, t, z, fprev, x, h, eps):
+    def svgd_iteration(self, prior, t, z, fprev, x, h, eps, kernel=KERNEL_RBF):
         fprev = _f64(fprev).reshape(-1, self.d); x = _f64(x).reshape(-1, self.d).copy(); z = _f64(z)
         lib().om_svgd_iteration(self.ref, int(prior), int(t), _dp(z), _dp(fprev), fprev.shape[0],
-                                _dp(x), x.shape[0], float(h), float(eps))
+                                _dp(x), x.shape[0], float(h), float(eps), int(kernel))
         return x
 
-    def svgd_iters(self, prior, bw_rule, bw_value, t, z, fprev, x, L, eps):
+    def svgd_iters(self, prior, bw_rule, bw_value, t, z, fprev, x, L, eps, kernel=KERNEL_RBF):
         """L SVGD iterations from x (given f_t of the previous set). Returns (x, h[L])."""
         fprev = _f64(fprev).reshape(-1, self.d); x = _f64(x).reshape(-1, self.d).copy(); z = _f64(z)
         h = np.empty(max(int(L), 1))
         lib().om_svgd_iters(self.ref, int(prior), int(bw_rule), float(bw_value), int(t), _dp(z),
-                            _dp(fprev), fprev.shape[0], _dp(x), x.shape[0], int(L), float(eps), _dp(h))
+                            _dp(fprev), fprev.shape[0], _dp(x), x.shape[0], int(L), float(eps), _dp(h),
+                            int(kernel))
         return x, h[: int(L)]
 
     def forward(self, t, z, fprev, phi_prev, x):
@@ -230,7 +235,8 @@ def backtrack(x0, hist, psi, phiT):
     return path, idx, J
 
 
-def run_sequence(kind, params, N, L, eps, bw_rule, bw_value, prior, seed, seq, x0, z, T=None):
+def run_sequence(kind, params, N, L, eps, bw_rule, bw_value, prior, seed, seq, x0, z, T=None,
+                 kernel=KERNEL_RBF):
     """Algorithm 2 on one sequence. Returns dict(hist[T][N][d], psi[T][N], path[T+1][d], J)."""
     m = Model(kind, params)
     z = _f64(z).reshape(-1, m.dy)
@@ -238,7 +244,7 @@ def run_sequence(kind, params, N, L, eps, bw_rule, bw_value, prior, seed, seq, x
     z = np.ascontiguousarray(z[:T])
     params = m.params
     cfg = _RunCfg(m.kind, _dp(params), len(params), int(N), int(L), float(eps), int(bw_rule),
-                  float(bw_value), int(prior), ctypes.c_uint64(int(seed)))
+                  float(bw_value), int(prior), ctypes.c_uint64(int(seed)), int(kernel))
     x0 = _f64(x0)
     hist = np.empty((T, int(N), m.d)); psi = np.empty((T, int(N)), dtype=np.int32)
     path = np.empty((T + 1, m.d)); J = ctypes.c_double()
@@ -315,7 +321,7 @@ def proposal_features(kind, params, u, z):
 
 
 def run_batch(kind, params, N, L, eps, bw_rule, bw_value, prior, seed, seq_ids, x0, z, T,
-              nthreads=None):
+              nthreads=None, kernel=KERNEL_RBF):
     """Algorithm 2 on many sequences over host threads. z is [B][maxT][dy]."""
     m = Model(kind, params)
     seq_ids = np.ascontiguousarray(np.asarray(seq_ids, dtype=np.int32))
@@ -329,7 +335,7 @@ def run_batch(kind, params, N, L, eps, bw_rule, bw_value, prior, seed, seq_ids, 
     rc = lib().om_run_batch(m.kind, _dp(m.params), len(m.params), int(N), int(L), float(eps),
                             int(bw_rule), float(bw_value), int(prior), ctypes.c_uint64(int(seed)),
                             B, _ip(seq_ids), _dp(x0), maxT, _ip(T), _dp(z), _dp(path), _dp(J),
-                            nthreads)
+                            nthreads, int(kernel))
     if rc != 0:
         raise ValueError("oracle: run_batch rejected its input")
     return {"path": path, "J": J, "threads": min(max(nthreads, 1), 256)}

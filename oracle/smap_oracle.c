@@ -383,12 +383,32 @@ double om_bandwidth(const double* x, int N, int d, double scale)
     return scale * med / log((double)N);
 }
 
-/* RBF kernel and its gradient with respect to the second argument. */
-static double om_kappa(const double* a, const double* b, int d, double h)
+/* Stein kernels k(a, b) = k(r^2), r^2 = |a - b|^2, with bandwidth h:
+ *   RBF        exp(-r^2 / h)                         (Section V's kernel);
+ *   IMQ        (1 + r^2 / h)^(-1/2)                  (Gorham & Mackey 2017);
+ *   Matern 3/2 (1 + s) exp(-s), s = sqrt(3 r^2 / h)  (length scale sqrt(h)),
+ * the alternatives of the kernel ablation (Table Ex6). *kap = k(a, b) and
+ * *rho the factor with grad_b k(b, a) = rho (a - b), i.e. -2 dk/d(r^2):
+ * 2k/h, k^3/h and 3 exp(-s)/h respectively. */
+enum { OM_KERNEL_RBF = 0, OM_KERNEL_IMQ = 1, OM_KERNEL_MATERN32 = 2 };
+static void om_kernel(int kernel, const double* a, const double* b, int d, double h, double* kap,
+                      double* rho)
 {
-    double s = 0.0;
-    for (int c = 0; c < d; ++c) { double e = a[c] - b[c]; s += e * e; }
-    return exp(-s / h);
+    double r2 = 0.0;
+    for (int c = 0; c < d; ++c) { double e = a[c] - b[c]; r2 += e * e; }
+    if (kernel == OM_KERNEL_IMQ) {
+        double k = 1.0 / sqrt(1.0 + r2 / h);
+        *kap = k;
+        *rho = k * k * k / h;
+    } else if (kernel == OM_KERNEL_MATERN32) {
+        double sr = sqrt(3.0 * r2 / h), e = exp(-sr);
+        *kap = (1.0 + sr) * e;
+        *rho = 3.0 * e / h;
+    } else {
+        double k = exp(-r2 / h);
+        *kap = k;
+        *rho = 2.0 * k / h;
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -439,7 +459,7 @@ static void om_score(const om_model* m, int prior, int t, const double* z,
  * Eq. SVGD_initial_newupdate / SVGD_newupdate): all particles move together. */
 void om_svgd_iteration(const om_model* m, int prior, int t, const double* z,
                        const double* fprev, int Np, double* x, int N,
-                       double h, double eps)
+                       double h, double eps, int kernel)
 {
     int d = m->d;
     double* g = (double*)malloc(sizeof(double) * N * d);
@@ -449,10 +469,11 @@ void om_svgd_iteration(const om_model* m, int prior, int t, const double* z,
         const double* xi = x + (long)i * d;
         for (int k = 0; k < N; ++k) {
             const double* xk = x + (long)k * d;
-            double kap = om_kappa(xi, xk, d, h);
+            double kap, rho;
+            om_kernel(kernel, xi, xk, d, h, &kap, &rho);
             for (int c = 0; c < d; ++c) {
                 double drive = kap * g[(long)k * d + c];
-                double repulse = kap * (2.0 / h) * (xi[c] - xk[c]);  /* grad_{x_k} kappa */
+                double repulse = rho * (xi[c] - xk[c]);  /* grad_{x_k} kappa(x_k, x_i) */
                 phi[(long)i * d + c] += drive + repulse;
             }
         }
@@ -467,14 +488,14 @@ void om_svgd_iteration(const om_model* m, int prior, int t, const double* z,
  * h_out[l] receives the bandwidth used at iteration l (may be NULL). */
 void om_svgd_iters(const om_model* m, int prior, int bw_rule, double bw_value,
                    int t, const double* z, const double* fprev, int Np,
-                   double* x, int N, int L, double eps, double* h_out)
+                   double* x, int N, int L, double eps, double* h_out, int kernel)
 {
     double h = 1.0;
     for (int l = 0; l < L; ++l) {
         if (bw_rule == OM_BW_FIXED) h = bw_value;
         else if (bw_rule == OM_BW_MEDIAN_ITER || l == 0) h = om_bandwidth(x, N, m->d, bw_value);
         if (h_out) h_out[l] = h;
-        om_svgd_iteration(m, prior, t, z, fprev, Np, x, N, h, eps);
+        om_svgd_iteration(m, prior, t, z, fprev, Np, x, N, h, eps, kernel);
     }
 }
 
@@ -544,6 +565,7 @@ typedef struct {
     int kind; const double* params; int np;
     int N, L; double eps; int bw_rule; double bw_value; int prior;
     uint64_t seed;
+    int kernel;   /* OM_KERNEL_* */
 } om_run_cfg;
 
 /* Runs one sequence of length T. z is [T][dy]. Outputs (any may be NULL
@@ -577,7 +599,7 @@ int om_run_sequence(const om_run_cfg* cfg, uint32_t seq, const double* x0, int T
             for (int c = 0; c < d; ++c) x[(long)i * d + c] = fi[c] + sqrt(m.q[c]) * xi[c];
         }
         om_svgd_iters(&m, cfg->prior, cfg->bw_rule, cfg->bw_value, t, zt, fprev, Np,
-                      x, N, cfg->L, cfg->eps, NULL);
+                      x, N, cfg->L, cfg->eps, NULL, cfg->kernel);
         om_forward(&m, t, zt, fprev, Np, phi_prev, x, N, psi_t, phi);
         memcpy(H + (size_t)(t - 1) * N * d, x, sizeof(double) * N * d);
         memcpy(PSI + (size_t)(t - 1) * N, psi_t, sizeof(int) * N);
@@ -688,11 +710,11 @@ static void* om_worker(void* arg)
 int om_run_batch(int kind, const double* params, int np, int N, int L, double eps,
                  int bw_rule, double bw_value, int prior, uint64_t seed,
                  int nseq, const int* seq_ids, const double* x0, int maxT, const int* T,
-                 const double* z, double* path, double* J, int nthreads)
+                 const double* z, double* path, double* J, int nthreads, int kernel)
 {
     om_model m;
     if (om_setup(&m, kind, params, np)) return -1;
-    om_run_cfg cfg = { kind, params, np, N, L, eps, bw_rule, bw_value, prior, seed };
+    om_run_cfg cfg = { kind, params, np, N, L, eps, bw_rule, bw_value, prior, seed, kernel };
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
     pthread_t th[256];

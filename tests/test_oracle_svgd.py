@@ -116,3 +116,54 @@ def test_svgd_fixed_point_on_linear_gaussian(oracle):
     assert err < 1e-2 * resid
     # the unweighted mean is measurably off: the identity is specific to c_k
     assert np.abs(got.mean(0) - xs).max() > 10 * err
+
+
+# ----------------------------------------------- kernels of the ablation ----
+def _kernel_value(kernel, a, b, h):
+    """The kernels' definitions (RBF, IMQ with c = 1 and exponent -1/2,
+    Matern 3/2 with length scale sqrt(h)), for finite differences."""
+    r2 = float(np.sum((a - b) ** 2))
+    if kernel == 1:
+        return (1.0 + r2 / h) ** -0.5
+    if kernel == 2:
+        s = np.sqrt(3.0 * r2 / h)
+        return (1.0 + s) * np.exp(-s)
+    return np.exp(-r2 / h)
+
+
+@pytest.mark.parametrize("kernel", [0, 1, 2])
+def test_two_particles_repulsion_is_the_kernel_gradient(oracle, kernel):
+    """On a flat target (huge q and r) particle a moves by eps/2 times the
+    gradient of k(x_b, a) with respect to x_b: checked against central finite
+    differences of the kernel's definition, so the oracle's analytic gradient
+    of each kernel is pinned."""
+    m = _lin_model(oracle, 1e30, 1e30)
+    a, b = np.array([0.3, -0.2, 0.1, 0.0]), np.array([-0.1, 0.4, 0.2, 0.5])
+    eps = 0.01
+    h = np.sum((a - b) ** 2) / np.log(2.0)     # the median rule with one pair
+    got, hh = m.svgd_iters(0, 0, 1.0, 2, np.zeros(2), np.zeros((1, 4)), np.stack([a, b]), 1, eps, kernel=kernel)
+    assert hh[0] == pytest.approx(h, rel=1e-14)
+    step = 1e-6
+    fd = np.array([(_kernel_value(kernel, b + step * e, a, h) - _kernel_value(kernel, b - step * e, a, h)) / (2 * step)
+                   for e in np.eye(4)])
+    assert np.allclose(got[0] - a, eps * 0.5 * fd, rtol=1e-7, atol=1e-14)
+    assert np.allclose(got[1] - b, -(got[0] - a), rtol=1e-12, atol=1e-15)   # equal and opposite
+    assert np.sum((got[0] - got[1]) ** 2) > np.sum((a - b) ** 2)             # repulsive
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_other_kernels_keep_the_mean_and_weight_the_drive(oracle, kernel):
+    """Radial kernels: the repulsive sum is antisymmetric (flat target keeps the
+    particle mean); on a linear-Gaussian target one particle alone is plain
+    gradient ascent, as with the RBF kernel (k(x, x) = 1, zero gradient)."""
+    m = _lin_model(oracle, 1e30, 1e30)
+    x = np.random.default_rng(8).normal(0, 1, (17, 4))
+    got, _ = m.svgd_iters(0, 0, 1.0, 2, np.zeros(2), np.zeros((1, 4)), x, 5, 0.05, kernel=kernel)
+    assert np.allclose(got.mean(0), x.mean(0), rtol=0, atol=1e-13)
+    assert not np.allclose(got, x)
+    m2 = _lin_model(oracle, 0.01, 0.05)
+    x1 = np.array([[0.2, -0.1, 0.3, 0.05]])
+    z = np.array([0.1, -0.2]); fprev = np.zeros((1, 4))
+    r_rbf, _ = m2.svgd_iters(0, 0, 1.0, 2, z, fprev, x1, 3, 0.002)
+    r_k, _ = m2.svgd_iters(0, 0, 1.0, 2, z, fprev, x1, 3, 0.002, kernel=kernel)
+    assert np.array_equal(r_rbf, r_k)
