@@ -91,6 +91,14 @@ typedef enum { SMAP_BW_MEDIAN_ITER = 0, SMAP_BW_MEDIAN_STEP = 1, SMAP_BW_FIXED =
  * They coincide when the previous set has one particle (t = 1). */
 typedef enum { SMAP_PRIOR_MIXTURE = 0, SMAP_PRIOR_MEANGRAD = 1 } smap_prior;
 
+/* Stein kernel k(x, x') of the SVGD direction (Eq. svgd_iterate), u = r^2 / h
+ * with r = |x - x'| and h the bandwidth of smap_bw_rule:
+ *   RBF        exp(-u)                            (the method's kernel, Section V)
+ *   IMQ        (1 + u)^(-1/2)                     (Gorham & Mackey 2017)
+ *   MATERN32   (1 + s) exp(-s), s = sqrt(3 u)     (Matern nu = 3/2, length sqrt(h))
+ * IMQ and Matern are the alternatives of the kernel ablation (Table Ex6). */
+typedef enum { SMAP_KERNEL_RBF = 0, SMAP_KERNEL_IMQ = 1, SMAP_KERNEL_MATERN32 = 2 } smap_kernel;
+
 typedef struct smap_handle smap_handle;
 
 typedef struct {
@@ -107,7 +115,8 @@ typedef struct {
     int batch;              /* number of independent sequences B >= 1 */
     int max_T;              /* longest sequence the handle can hold */
     const double* x0;       /* host [batch][d]: the known initial states x_0^true */
-    void* stream;           /* cudaStream_t (NULL = legacy default stream) */
+    void* stream;           /* cudaStream_t the handle works on; NULL: the handle creates its own */
+    int kernel;             /* smap_kernel (0 = RBF) */
 } smap_config;
 
 /* Validates cfg, allocates the handle's device buffers (particle history

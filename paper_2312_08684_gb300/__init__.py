@@ -18,19 +18,19 @@ class Estimator:
     """One smap handle: B sequences, N particles, L SVGD iterations per step."""
 
     def __init__(self, kind, params, N, L, step, x0, max_T, bw_rule=0, bw_value=1.0, prior=0,
-                 seed=1, stream=None):
+                 seed=1, stream=None, kernel=0):
         x0 = np.ascontiguousarray(x0, np.float64)
         self.B = int(x0.shape[0])
         self.N, self.L, self.max_T = int(N), int(L), int(max_T)
         self.h = abi.smap_create(kind, params, N, L, step, bw_rule, bw_value, prior, seed, self.B,
-                                 max_T, x0, stream)
+                                 max_T, x0, stream, kernel)
         self.d, self.dy = abi.smap_dims(self.h)
 
     @classmethod
     def from_workload(cls, wl, stream=None, **over):
         kw = dict(kind=wl.kind, params=wl.params, N=wl.N, L=wl.L, step=wl.step, x0=wl.x0,
                   max_T=wl.maxT, bw_rule=wl.bw_rule, bw_value=wl.bw_value, prior=wl.prior,
-                  seed=wl.seed, stream=stream)
+                  seed=wl.seed, stream=stream, kernel=wl.kernel)
         kw.update(over)
         return cls(**kw)
 

@@ -51,7 +51,7 @@ class smap_config(ctypes.Structure):
         ("N", ctypes.c_int), ("L", ctypes.c_int), ("step", ctypes.c_double),
         ("bw_rule", ctypes.c_int), ("bw_value", ctypes.c_double), ("prior", ctypes.c_int),
         ("seed", ctypes.c_uint64), ("batch", ctypes.c_int), ("max_T", ctypes.c_int),
-        ("x0", ctypes.POINTER(ctypes.c_double)), ("stream", ctypes.c_void_p),
+        ("x0", ctypes.POINTER(ctypes.c_double)), ("stream", ctypes.c_void_p), ("kernel", ctypes.c_int),
     ]
 
 
@@ -175,14 +175,14 @@ def _stream_ptr(stream):
 
 # ---------------------------------------------------------------- calls ----
 def smap_create(model, params, N, L, step, bw_rule, bw_value, prior, seed, batch, max_T, x0,
-                stream=None):
+                stream=None, kernel=0):
     lib = load()
     params = np.ascontiguousarray(params, dtype=np.float64).ravel()
     x0 = np.ascontiguousarray(x0, dtype=np.float64)
     cfg = smap_config(int(model), params.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(params),
                       int(N), int(L), float(step), int(bw_rule), float(bw_value), int(prior),
                       ctypes.c_uint64(int(seed)), int(batch), int(max_T),
-                      x0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream_ptr(stream))
+                      x0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream_ptr(stream), int(kernel))
     h = ctypes.c_void_p()
     st = lib.smap_create(ctypes.byref(cfg), ctypes.byref(h))
     if st != SMAP_OK:

@@ -327,6 +327,7 @@ smap_status launch_seq(smap_handle* h, int v, int items, int mode, const float* 
     a.L = h->cfg.L;
     a.bw_rule = h->cfg.bw_rule;
     a.prior = h->cfg.prior;
+    a.kernel = h->cfg.kernel;
     a.mode = mode;
     a.eps = (float)h->cfg.step;
     a.bw_value = (float)h->cfg.bw_value;
@@ -657,6 +658,7 @@ smap_status smap_create(const smap_config* cfg, smap_handle** out) {
     if (cfg->bw_rule < 0 || cfg->bw_rule > 2) return bail(SMAP_E_INVAL, "bw_rule");
     if (!(cfg->bw_value > 0) || !std::isfinite(cfg->bw_value)) return bail(SMAP_E_INVAL, "bw_value must be > 0");
     if (cfg->prior < 0 || cfg->prior > 1) return bail(SMAP_E_INVAL, "prior");
+    if (cfg->kernel < 0 || cfg->kernel > 2) return bail(SMAP_E_INVAL, "kernel");
     if (!cfg->x0) return bail(SMAP_E_INVAL, "x0 is null");
     h->B = cfg->batch;
     h->Nmax = cfg->N;
@@ -1004,7 +1006,7 @@ smap_status smap_debug_svgd(smap_handle* h, int t, const float* x_prev, int n_pr
     memset(&a, 0, sizeof(a));
     a.mp = h->mp;
     a.B = (int)B; a.N = (int)N; a.Np = n_prev; a.t = t; a.iters = n_iters;
-    a.bw_rule = h->cfg.bw_rule; a.prior = h->cfg.prior;
+    a.bw_rule = h->cfg.bw_rule; a.prior = h->cfg.prior; a.kernel = h->cfg.kernel;
     a.eps = (float)h->cfg.step; a.bw_value = (float)h->cfg.bw_value;
     a.xprev = dxp; a.x0 = h->x0; a.xinit = dxi; a.y = dy; a.xout = dxo; a.hout = dho; a.f64 = df;
     const int v = h->variant >= 0 ? h->variant : heuristic_variant(h);

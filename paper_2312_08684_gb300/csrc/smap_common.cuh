@@ -56,6 +56,7 @@ struct SeqArgs {
     int y_full;               // mode 1: y is [B][maxT][dy] (indexed by the step)
     int skip_done;            // mode 1: skip sequences with tcur >= Tend
     int seq_base;             // without `order`, item k is sequence seq_base + k
+    int kernel;               // Stein kernel: 0 RBF, 1 IMQ, 2 Matern 3/2
 };
 
 // Arguments of the debug SVGD kernel.
@@ -70,6 +71,7 @@ struct DebugSvgdArgs {
     float* xout;              // [B][N][d]
     float* hout;              // [B][iters]
     double* f64;              // [B][Np][d] scratch
+    int kernel;               // Stein kernel: 0 RBF, 1 IMQ, 2 Matern 3/2
 };
 
 // ex2.approx: 2^x on the special-function unit (max rel. error ~2^-22).

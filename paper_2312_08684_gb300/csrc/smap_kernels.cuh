@@ -731,12 +731,82 @@ __device__ __forceinline__ void rbf_update(const Sm& s, int N, float Bc) {
     __syncthreads();
 }
 
+// a5 for the other Stein kernels of the kernel ablation (Table Ex6), as
+// functions of u = r^2 / h = |x^_i - x^_k|^2 ln 2:
+//   KER 1, IMQ         kappa = (1 + u)^-1/2,            repulsion weight kappa^3
+//   KER 2, Matern 3/2  kappa = (1 + s) e^-s, s = sqrt(3u), repulsion weight e^-s
+// The drive (gs = A g_k) and the repulsion Bk (x^_i sum rho - sum rho x^_k)
+// accumulate separately, their weights differing.
+template <class M, int PPT, int KER>
+__device__ __forceinline__ void kernel_update(const Sm& s, int N, float Bk) {
+    constexpr int D = M::D, DP = M::DP;
+    constexpr float kLn2 = 0.6931471805599453f;
+    const int tid = threadIdx.x, NT = blockDim.x;
+    float xi[PPT][D], ni[PPT], Sg[PPT][D], Sx[PPT][D], Sr[PPT];
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        const int i = min(tid + p * NT, N - 1);
+        load_row<D, DP>(s.xs, i, xi[p]);
+        ni[p] = -s.nrm[i];
+        Sr[p] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            xi[p][c] *= 2.0f;
+            Sg[p][c] = 0.0f;
+            Sx[p][c] = 0.0f;
+        }
+    }
+#pragma unroll 2
+    for (int k = 0; k < N; ++k) {
+        float xk[D], gk[D];
+        load_row<D, DP>(s.xs, k, xk);
+        load_row<D, DP>(s.gs, k, gk);
+        const float nk = s.nrm[k];
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            float m = ni[p] - nk;   // -|x^_i - x^_k|^2
+#pragma unroll
+            for (int c = 0; c < D; ++c) m = fmaf(xi[p][c], xk[c], m);
+            const float u = fmaxf(-m, 0.0f) * kLn2;
+            float kap, rho;
+            if constexpr (KER == 1) {
+                kap = rsqrtf(1.0f + u);
+                rho = kap * kap * kap;
+            } else {
+                const float sq = sqrtf(3.0f * u);
+                rho = fast_exp2(-sq * kL2E);
+                kap = fmaf(sq, rho, rho);
+            }
+            Sr[p] += rho;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                Sg[p][c] = fmaf(kap, gk[c], Sg[p][c]);
+                Sx[p][c] = fmaf(rho, xk[c], Sx[p][c]);
+            }
+        }
+    }
+    __syncthreads();   // every thread is done reading xs / gs / nrm
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        const int i = tid + p * NT;
+        if (i >= N) continue;
+        float xn[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const float x = 0.5f * xi[p][c];
+            xn[c] = x + Sg[p][c] + Bk * fmaf(x, Sr[p], -Sx[p][c]);
+        }
+        store_row<D, DP>(s.xs, i, xn);
+    }
+    __syncthreads();
+}
+
 // a3..a6: L iterations on the absolute particles in xs (left absolute on
 // return). hout (may be null) receives h per iteration.
 template <class M, int PPT>
 __device__ void svgd_iterations(const ModelParams& mp, const Sm& s, int N, int Np, int L, float eps,
                                 int bw_rule, float bw_value, int prior, MedState& st, float q_extra,
-                                float* hout, int* stats) {
+                                float* hout, int* stats, int kernel) {
     constexpr int D = M::D, DP = M::DP;
     if (L <= 0) return;
     const int tid = threadIdx.x, NT = blockDim.x;
@@ -772,10 +842,14 @@ __device__ void svgd_iterations(const ModelParams& mp, const Sm& s, int N, int N
         const float sc_new = sqrtf(kL2E / h);
         const float A = sc_new * eps / (float)N;
         const float Bc = 2.0f * eps / ((float)N * h);
-        rescale_and_score<M, PPT>(mp, s, N, Np, prior, sc_new / sc, 1.0f / sc_new, A, Bc);
+        // RBF: the update is regrouped around w_k = A g_k - Bc x^_k; the
+        // other kernels keep A g_k and add their repulsion separately
+        rescale_and_score<M, PPT>(mp, s, N, Np, prior, sc_new / sc, 1.0f / sc_new, A, kernel == 0 ? Bc : 0.0f);
         sc = sc_new;
         __syncthreads();
-        rbf_update<M, PPT>(s, N, Bc);
+        if (kernel == 1) kernel_update<M, PPT, 1>(s, N, eps / ((float)N * h));
+        else if (kernel == 2) kernel_update<M, PPT, 2>(s, N, 3.0f * eps / ((float)N * h));
+        else rbf_update<M, PPT>(s, N, Bc);
     }
     // back to absolute coordinates
     const float inv = 1.0f / sc;
@@ -1011,7 +1085,7 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
             if (!a.viterbi_only) {
                 st.fresh = 1;
                 svgd_iterations<M, PPT>(mp, s, N, Np, a.L, a.eps, a.bw_rule, a.bw_value, a.prior, st,
-                                        q_extra, nullptr, a.stats);
+                                        q_extra, nullptr, a.stats, a.kernel);
             }
             int best[PPT];
             double phinew[PPT];
@@ -1076,7 +1150,7 @@ __global__ void __launch_bounds__(MAXT, MINB) debug_svgd_kernel(const __grid_con
     st.w = 0.004f;
     st.fresh = 1;
     svgd_iterations<M, PPT>(a.mp, s, a.N, a.Np, a.iters, a.eps, a.bw_rule, a.bw_value, a.prior, st,
-                            init_spread(a.mp), a.hout ? a.hout + (size_t)b * a.iters : nullptr, nullptr);
+                            init_spread(a.mp), a.hout ? a.hout + (size_t)b * a.iters : nullptr, nullptr, a.kernel);
     for (int e = tid; e < a.N * D; e += NT)
         a.xout[(size_t)b * a.N * D + e] = s.xs[(e / D) * DP + (e % D)];
 }

@@ -53,6 +53,7 @@ class Workload:
     T: np.ndarray             # [B] int32 sequence lengths
     Nseq: np.ndarray          # [B] int32 particles per sequence
     truth: np.ndarray         # [B][maxT+1][d] float64 simulated states
+    kernel: int = 0           # Stein kernel: 0 RBF, 1 IMQ, 2 Matern 3/2
 
     @property
     def B(self) -> int:

@@ -61,11 +61,11 @@ CASES = {
 SPREAD = {"ngm1d": 2.0, "range": 0.3, "clutter": 0.3, "arm": 0.02, "linear": 0.2}
 
 
-def _svgd_case(oracle, name, t, n_iters, prior=0, bw_rule=0, bw_value=1.0, N=None):
+def _svgd_case(oracle, name, t, n_iters, prior=0, bw_rule=0, bw_value=1.0, N=None, kernel=0):
     wl = CASES[name]()
     if N is not None:
         wl.N = N
-    wl.prior, wl.bw_rule, wl.bw_value = prior, bw_rule, bw_value
+    wl.prior, wl.bw_rule, wl.bw_value, wl.kernel = prior, bw_rule, bw_value, kernel
     m = oracle.Model(wl.kind, wl.params)
     rng = np.random.default_rng(t * 100 + wl.N)
     B, N, d = wl.B, wl.N, wl.d
@@ -85,7 +85,7 @@ def _svgd_case(oracle, name, t, n_iters, prior=0, bw_rule=0, bw_value=1.0, N=Non
         xg, hg = est.debug_svgd(t, xprev, xinit, y, n_iters)
     for b in range(B):
         xo, ho = m.svgd_iters(prior, bw_rule, bw_value, t, y[b].astype(np.float64), fprev[b],
-                              xinit[b].astype(np.float64), n_iters, wl.step)
+                              xinit[b].astype(np.float64), n_iters, wl.step, kernel=kernel)
         yield b, xg[b], xo, hg[b], ho
 
 
@@ -117,6 +117,17 @@ def test_particle_counts_edge_cases(oracle, N):
     """N = 1 (gradient ascent), 2, odd / ragged counts around a warp, > 256."""
     for b, xg, xo, hg, ho in _svgd_case(oracle, "linear", 2, 1, N=N):
         assert rel_err(xg, xo) <= 1e-5
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("name", ["ngm1d", "range", "clutter", "arm"])
+def test_ablation_kernels_match_oracle(oracle, name, kernel):
+    """IMQ and Matern 3/2 Stein kernels (Table Ex6's alternatives): one
+    iteration at t = 1 and t = 3, GPU vs oracle."""
+    for t in (1, 3):
+        for b, xg, xo, hg, ho in _svgd_case(oracle, name, t, 1, kernel=kernel):
+            assert np.allclose(hg, ho, rtol=1e-5), (hg, ho)
+            assert rel_err(xg, xo) <= 1e-5, (name, kernel, t, b, rel_err(xg, xo))
 
 
 def test_many_iterations_stay_close(oracle):
@@ -178,7 +189,7 @@ def _run_gpu(wl, **kw):
 def _run_oracle(oracle, wl, b):
     return oracle.run_sequence(wl.kind, wl.params, int(wl.Nseq[b]), wl.L, wl.step, wl.bw_rule,
                                wl.bw_value, wl.prior, wl.seed, b, wl.x0[b],
-                               wl.y[b, : wl.T[b]].astype(np.float64))
+                               wl.y[b, : wl.T[b]].astype(np.float64), kernel=wl.kernel)
 
 
 def test_full_run_ngm1d_matches_oracle(oracle):
@@ -203,6 +214,18 @@ def test_full_run_small_matches_oracle(oracle, name):
         assert rel_err(path[b, : T + 1], ref["path"]) <= 1e-3
         assert J[b] == pytest.approx(ref["J"], rel=1e-3)
         assert np.all(np.isnan(path[b, T + 1:]))
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_ablation_kernels_full_run_matches_oracle(oracle, kernel):
+    wl = W.make_range_cv(B=2, T=12, N=48, L=10, dropout=(4, 7))
+    wl.kernel = kernel
+    path, J, hist, psi = _run_gpu(wl)
+    for b in range(wl.B):
+        ref = _run_oracle(oracle, wl, b)
+        assert rel_err(hist[b], ref["hist"]) <= 1e-3
+        assert rel_err(path[b], ref["path"]) <= 1e-3
+        assert J[b] == pytest.approx(ref["J"], rel=1e-3)
 
 
 def test_step_loop_equals_batched_graph_run():
