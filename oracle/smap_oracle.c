@@ -48,7 +48,7 @@
 #define OM_MAXP 128
 
 enum { OM_NGM1D = 1, OM_RANGE_CV2D = 2, OM_CLUTTER_CV2D = 3, OM_PLANAR_ARM = 4,
-       OM_LINEAR_GAUSS = 5 };
+       OM_LINEAR_GAUSS = 5, OM_RANGE_ZV2D = 6 };
 enum { OM_BW_MEDIAN_ITER = 0, OM_BW_MEDIAN_STEP = 1, OM_BW_FIXED = 2 };
 enum { OM_PRIOR_MIXTURE = 0, OM_PRIOR_MEANGRAD = 1 };
 
@@ -75,6 +75,9 @@ typedef struct {
 /*               state (angles, rates); z = sum_l len_l (cos th_l, sin th_l) */
 /*               th_l = sum_{m<=l} angle_m, noise N(0, r I_2)                 */
 /*  LINEAR_GAUSS [dt, q0..q3, r]; constant velocity, z = p + N(0, r I_2)      */
+/*  RANGE_ZV2D   [q0, q1, r, nb, b0x, b0y, ...]  state (px, py); zero-velocity */
+/*               random walk x_t = x_{t-1} + v (Section V-C's target model);  */
+/*               z_l = ||p - b_l|| + N(0, r); NaN = anchor not heard          */
 /* ------------------------------------------------------------------------ */
 
 int om_setup(om_model* m, int kind, const double* p, int np)
@@ -118,6 +121,14 @@ int om_setup(om_model* m, int kind, const double* p, int np)
         m->d = 4; m->dy = 2;
         for (int k = 0; k < 4; ++k) m->q[k] = p[1 + k];
         break;
+    case OM_RANGE_ZV2D: {
+        if (np < 4) return -1;
+        int nb = (int)p[3];
+        if (nb < 1 || nb > 8 || np != 4 + 2 * nb) return -1;
+        m->d = 2; m->dy = nb;
+        m->q[0] = p[0]; m->q[1] = p[1];
+        break;
+    }
     default:
         return -1;
     }
@@ -144,6 +155,10 @@ void om_transition(const om_model* m, int t, const double* x, double* f)
         f[3] = x[3];
         break;
     }
+    case OM_RANGE_ZV2D:
+        f[0] = x[0];
+        f[1] = x[1];
+        break;
     case OM_PLANAR_ARM: {
         int nl = (int)p[1];
         double dt = p[0];
@@ -189,6 +204,31 @@ static double om_lognorm1(double v, double s)
 }
 
 /* log p(z_t | x_t) (Eq. SSM-z). */
+/* Range measurements to nb anchors b (x, y pairs), variance r: the log
+ * likelihood and its gradient in the position (x[0], x[1]); NaN = not heard. */
+static double om_range_loglik(const double* x, const double* z, int nb, double r, const double* b)
+{
+    double s = 0.0;
+    for (int l = 0; l < nb; ++l) {
+        if (isnan(z[l])) continue;
+        double dx = x[0] - b[2 * l], dy = x[1] - b[2 * l + 1];
+        s += om_lognorm1(z[l] - sqrt(dx * dx + dy * dy), r);
+    }
+    return s;
+}
+static void om_range_grad(const double* x, const double* z, int nb, double r, const double* b, double* g)
+{
+    for (int l = 0; l < nb; ++l) {
+        if (isnan(z[l])) continue;
+        double dx = x[0] - b[2 * l], dy = x[1] - b[2 * l + 1];
+        double rho = sqrt(dx * dx + dy * dy);
+        if (rho < 1e-9) rho = 1e-9;
+        double c = (z[l] - rho) / r / rho;
+        g[0] += c * dx;
+        g[1] += c * dy;
+    }
+}
+
 double om_loglik(const om_model* m, int t, const double* z, const double* x)
 {
     const double* p = m->p;
@@ -196,17 +236,10 @@ double om_loglik(const om_model* m, int t, const double* z, const double* x)
     switch (m->kind) {
     case OM_NGM1D:
         return om_lognorm1(z[0] - p[7] * x[0] * x[0], p[6]);
-    case OM_RANGE_CV2D: {
-        int nb = (int)p[6];
-        double r = p[5], s = 0.0;
-        for (int l = 0; l < nb; ++l) {
-            if (isnan(z[l])) continue;          /* beacon not heard at this step */
-            double dx = x[0] - p[7 + 2 * l], dy = x[1] - p[8 + 2 * l];
-            double rho = sqrt(dx * dx + dy * dy);
-            s += om_lognorm1(z[l] - rho, r);
-        }
-        return s;
-    }
+    case OM_RANGE_CV2D:
+        return om_range_loglik(x, z, (int)p[6], p[5], p + 7);
+    case OM_RANGE_ZV2D:
+        return om_range_loglik(x, z, (int)p[3], p[2], p + 4);
     case OM_CLUTTER_CV2D: {
         double r = p[5], beta = p[7], area = p[8];
         int M = (int)p[6];
@@ -247,20 +280,12 @@ void om_grad_loglik(const om_model* m, int t, const double* z, const double* x, 
         g[0] = res / p[6] * 2.0 * p[7] * x[0];
         break;
     }
-    case OM_RANGE_CV2D: {
-        int nb = (int)p[6];
-        double r = p[5];
-        for (int l = 0; l < nb; ++l) {
-            if (isnan(z[l])) continue;
-            double dx = x[0] - p[7 + 2 * l], dy = x[1] - p[8 + 2 * l];
-            double rho = sqrt(dx * dx + dy * dy);
-            if (rho < 1e-9) rho = 1e-9;
-            double c = (z[l] - rho) / r / rho;
-            g[0] += c * dx;
-            g[1] += c * dy;
-        }
+    case OM_RANGE_CV2D:
+        om_range_grad(x, z, (int)p[6], p[5], p + 7, g);
         break;
-    }
+    case OM_RANGE_ZV2D:
+        om_range_grad(x, z, (int)p[3], p[2], p + 4, g);
+        break;
     case OM_CLUTTER_CV2D: {
         double r = p[5], beta = p[7], area = p[8];
         int M = (int)p[6];

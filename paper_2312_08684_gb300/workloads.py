@@ -19,6 +19,10 @@ Workloads (sizes can be shrunk for tests; the default sizes are the full ones):
               N=1024, L=50, T=100, B=256.                           (Section V-D form)
   linear_gauss constant velocity with direct position measurements: the
               linear-Gaussian case used by the smoother check.
+  range_zv    2-D position without a motion prior (zero-velocity random walk,
+              q = (1.0 * 0.1)^2), range-only to 3 anchors (sigma 0.5), anchor 1
+              silent in six periods of 25-50 steps, T=600 at 10 Hz, N=40,
+              L=100.                                                 (Section V-C form)
 Parameter-vector layouts are the ones documented in include/smap.h.
 """
 from __future__ import annotations
@@ -30,6 +34,7 @@ import numpy as np
 BASE_SEED = 20231208
 
 MODEL_NGM1D, MODEL_RANGE_CV2D, MODEL_CLUTTER_CV2D, MODEL_PLANAR_ARM, MODEL_LINEAR_GAUSS = 1, 2, 3, 4, 5
+MODEL_RANGE_ZV2D = 6
 BW_MEDIAN_ITER, BW_MEDIAN_STEP, BW_FIXED = 0, 1, 2
 PRIOR_MIXTURE, PRIOR_MEANGRAD = 0, 1
 
@@ -238,3 +243,36 @@ FULL = {
     "clutter_cv": lambda: make_clutter_cv(),
     "planar_arm": lambda: make_planar_arm(),
 }
+
+
+# ------------------------------------------------------------- range_zv ----
+ZV_ANCHORS = np.array([[5.0, 10.0], [0.0, 0.0], [10.0, 0.0]])
+# (first step, length) of the periods in which anchor 1 is not heard; the
+# lengths are Section V-C's blocking durations (2.5 .. 5 s at 10 Hz)
+ZV_BLOCKED = ((50, 25), (150, 50), (250, 40), (350, 40), (450, 30), (530, 35))
+
+
+def zv_params(anchors=ZV_ANCHORS, q=0.01, r=0.25) -> np.ndarray:
+    anchors = np.asarray(anchors, np.float64)
+    return np.concatenate([[q, q, r, len(anchors)], anchors.ravel()])
+
+
+def make_range_zv(B=1, T=600, N=40, L=100, step=0.005, seed=6, blocked=ZV_BLOCKED, bw_value=1.0,
+                  prior=PRIOR_MIXTURE, first=0) -> Workload:
+    p = zv_params()
+    q, r = p[0], p[2]
+    anchors = p[4:].reshape(-1, 2)
+    x0 = np.zeros((B, 2)); y = np.zeros((B, T, len(anchors)), np.float32); truth = np.zeros((B, T + 1, 2))
+    for s in range(B):
+        g = _rng(6, first + s)
+        x = np.array([5.0, 4.0]) + g.normal(0.0, 0.5, 2)
+        x0[s] = x
+        truth[s, 0] = x
+        for t in range(1, T + 1):
+            x = x + g.normal(0.0, np.sqrt(q), 2)
+            truth[s, t] = x
+            y[s, t - 1] = np.linalg.norm(anchors - x, axis=1) + g.normal(0.0, np.sqrt(r), len(anchors))
+        for t0, n in blocked or ():
+            y[s, t0:min(T, t0 + n), 0] = np.nan
+    return Workload("range_zv", MODEL_RANGE_ZV2D, p, 2, len(anchors), N, L, step, BW_MEDIAN_ITER, bw_value,
+                    prior, seed, x0, y, np.full(B, T, np.int32), np.full(B, N, np.int32), truth)

@@ -27,6 +27,7 @@ def _models(O):
                 lambda r: r.normal(0, 1.0, 2)),
         "linear": (O.Model(5, W.linear_params()), lambda r: np.r_[r.normal(0, 3, 2), r.normal(0, 1, 2)],
                    lambda r: r.normal(0, 3, 2)),
+        "range_zv": (O.Model(6, W.zv_params()), lambda r: r.uniform(-2, 12, 2), lambda r: r.uniform(0, 14, 3)),
     }
 
 
@@ -93,6 +94,15 @@ def test_loglik_against_scipy(oracle):
         z = np.array([e.real, e.imag]) + rng.normal(0, 0.02, 2)
         ref = stats.multivariate_normal.logpdf(z, [e.real, e.imag], 1e-4 * np.eye(2))
         assert m.loglik(1, z, x) == pytest.approx(ref, rel=1e-10)
+    # RANGE_ZV2D: the same range product for a 2-D position
+    m = oracle.Model(6, W.zv_params())
+    for _ in range(20):
+        x = rng.uniform(-2, 12, 2)
+        z = rng.uniform(0, 14, 3)
+        rho = np.linalg.norm(x - W.ZV_ANCHORS, axis=1)
+        assert m.loglik(1, z, x) == pytest.approx(stats.norm.logpdf(z, rho, 0.5).sum(), rel=1e-12)
+        z2 = z.copy(); z2[0] = np.nan
+        assert m.loglik(1, z2, x) == pytest.approx(stats.norm.logpdf(z[1:], rho[1:], 0.5).sum(), rel=1e-12)
     # LINEAR_GAUSS
     m = oracle.Model(5, W.linear_params())
     x = rng.normal(0, 1, 4); z = rng.normal(0, 1, 2)
@@ -112,6 +122,12 @@ def test_logtrans_and_transition_against_scipy(oracle):
     F = np.block([[np.eye(2), 0.1 * np.eye(2)], [np.zeros((2, 2)), np.eye(2)]])
     x = rng.normal(0, 1, 4)
     assert np.allclose(m.transition(5, x), F @ x, rtol=0, atol=1e-15)
+    # zero-velocity random walk: the identity, with density N(x; f, 0.01 I)
+    m = oracle.Model(6, W.zv_params())
+    x = rng.normal(0, 3, 2)
+    assert np.array_equal(m.transition(7, x), x)
+    f = rng.normal(0, 3, 2)
+    assert m.logtrans(x, f) == pytest.approx(stats.multivariate_normal.logpdf(x, f, 0.01 * np.eye(2)), rel=1e-12)
     # NGM1D time dependence: cos(1.2 t) in the workload form, cos(1.2 (t-1)) in the paper's
     m = oracle.Model(1, W.ngm1d_params())
     assert m.transition(3, [2.0])[0] == pytest.approx(1.0 + 50.0 / 5.0 + 8 * np.cos(3.6), rel=1e-14)
@@ -119,7 +135,7 @@ def test_logtrans_and_transition_against_scipy(oracle):
     assert m.transition(3, [2.0])[0] == pytest.approx(1.8 + 20.0 / 5.0 + 8 * np.cos(2.4), rel=1e-14)
 
 
-@pytest.mark.parametrize("name", ["ngm1d", "ngm1d_paper", "range", "clutter", "arm", "linear"])
+@pytest.mark.parametrize("name", ["ngm1d", "ngm1d_paper", "range", "clutter", "arm", "linear", "range_zv"])
 def test_grad_loglik_finite_differences(oracle, name):
     m, xs, zs = _models(oracle)[name]
     rng = np.random.default_rng(3)
