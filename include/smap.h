@@ -66,13 +66,18 @@ typedef enum {
  *      this build compiles nl = 7)
  *  SMAP_MODEL_LINEAR_GAUSS [dt, q0, q1, q2, q3, r]                     d=4, dy=2
  *      constant velocity, z = (px, py) + N(0, r I)
+ *  SMAP_MODEL_RANGE_ZV2D   [q0, q1, r, nb, a0x, a0y, ...]               d=2, dy=nb (1..8)
+ *      state (px, py) without a motion prior: x_t = x_{t-1} + N(0, diag(q0, q1));
+ *      z_l = ||x - a_l|| + N(0, r), NaN = anchor l not heard (Section V-C's
+ *      zero-velocity model)
  */
 typedef enum {
     SMAP_MODEL_NGM1D = 1,
     SMAP_MODEL_RANGE_CV2D = 2,
     SMAP_MODEL_CLUTTER_CV2D = 3,
     SMAP_MODEL_PLANAR_ARM = 4,
-    SMAP_MODEL_LINEAR_GAUSS = 5
+    SMAP_MODEL_LINEAR_GAUSS = 5,
+    SMAP_MODEL_RANGE_ZV2D = 6
 } smap_model;
 
 /* Kernel bandwidth h of kappa(x,x') = exp(-||x-x'||^2 / h) (the RBF kernel of

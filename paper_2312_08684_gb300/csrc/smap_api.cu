@@ -90,7 +90,7 @@ __global__ void normals_kernel(uint64_t seed, uint32_t seq, uint32_t t, uint32_t
 }
 
 const ModelKernels* kernels_for(int kind) {
-    static ModelKernels tab[6];
+    static ModelKernels tab[7];
     static bool init = false;
     if (!init) {
         tab[1] = kernels_ngm1d();
@@ -98,9 +98,10 @@ const ModelKernels* kernels_for(int kind) {
         tab[3] = kernels_clutter_cv();
         tab[4] = kernels_planar_arm7();
         tab[5] = kernels_linear_gauss();
+        tab[6] = kernels_range_zv();
         init = true;
     }
-    if (kind < 1 || kind > 5) return nullptr;
+    if (kind < 1 || kind > 6) return nullptr;
     return &tab[kind];
 }
 
@@ -149,6 +150,15 @@ bool make_model(int kind, const double* p, int np, ModelParams& mp, std::string&
         mp.d = 2 * nl; mp.dy = 2;
         for (int c = 0; c < 2 * nl; ++c) mp.q[c] = p[3 + c];
         mp.aux[0] = -std::log(two_pi * p[2]); mp.auxf[0] = (float)(1.0 / p[2]);
+        break;
+    }
+    case SMAP_MODEL_RANGE_ZV2D: {
+        const int nb = np >= 4 ? (int)p[3] : 0;
+        if (nb < 1 || nb > 8 || np != 4 + 2 * nb) { err = "RANGE_ZV2D: expects 4 + 2 nb parameters, nb 1..8"; return false; }
+        if (!(p[2] > 0)) { err = "RANGE_ZV2D: r must be > 0"; return false; }
+        mp.d = 2; mp.dy = nb;
+        mp.q[0] = p[0]; mp.q[1] = p[1];
+        mp.aux[0] = -0.5 * std::log(two_pi * p[2]); mp.auxf[0] = (float)(1.0 / p[2]);
         break;
     }
     case SMAP_MODEL_LINEAR_GAUSS:

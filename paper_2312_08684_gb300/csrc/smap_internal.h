@@ -28,6 +28,7 @@ ModelKernels kernels_range_cv();
 ModelKernels kernels_clutter_cv();
 ModelKernels kernels_planar_arm7();
 ModelKernels kernels_linear_gauss();
+ModelKernels kernels_range_zv();
 
 // Rows of the learned proposal: propagated particles u = f_t(x_{t-1}^i) + noise
 // (drawn exactly like the step kernels' initialisation) and their features.

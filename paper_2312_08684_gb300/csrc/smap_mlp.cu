@@ -458,6 +458,7 @@ const void* proposal_rows_fn(int kind) {
     case 3: return (const void*)proposal_rows_kernel<ModelClutterCV>;
     case 4: return (const void*)proposal_rows_kernel<ModelPlanarArm<7>>;
     case 5: return (const void*)proposal_rows_kernel<ModelLinearGauss>;
+    case 6: return (const void*)proposal_rows_kernel<ModelRangeZV>;
     }
     return nullptr;
 }

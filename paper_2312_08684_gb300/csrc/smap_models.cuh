@@ -61,6 +61,48 @@ struct CVTransition {
 
 // Range-only localisation. p = [dt, q0..q3, r, nb, b0x, b0y, ...].
 // aux[0] = -1/2 log(2 pi r), auxf[0] = 1/r. NaN observation = beacon not heard.
+// Section V-C's target without a motion prior: x = (px, py), zero-velocity
+// random walk x_t = x_{t-1} + v; ranges to nb anchors. Parameters
+// [q0, q1, r, nb, a0x, a0y, ...]; NaN = anchor not heard.
+struct ModelRangeZV {
+    static constexpr int KIND = 6, D = 2, DP = 2, DY = 8;
+    __device__ static double step_const(const ModelParams&, int) { return 0.0; }
+    __device__ static void transition(const ModelParams&, double, const float* x, float* f) {
+        f[0] = x[0];
+        f[1] = x[1];
+    }
+    __device__ static void transition64(const ModelParams&, double, const double* x, double* f) {
+        f[0] = x[0];
+        f[1] = x[1];
+    }
+    __device__ static void grad_loglik(const ModelParams& mp, const float* z, const float* x, float* g) {
+        const int nb = (int)mp.p[3];
+        float g0 = 0.0f, g1 = 0.0f;
+        for (int l = 0; l < nb; ++l) {
+            const float zl = z[l];
+            if (zl != zl) continue;
+            const float dx = x[0] - mp.pf[4 + 2 * l], dy = x[1] - mp.pf[5 + 2 * l];
+            const float rho = fmaxf(sqrtf(dx * dx + dy * dy), 1e-9f);
+            const float c = (zl - rho) * mp.auxf[0] / rho;
+            g0 = fmaf(c, dx, g0);
+            g1 = fmaf(c, dy, g1);
+        }
+        g[0] = g0; g[1] = g1;
+    }
+    __device__ static double loglik64(const ModelParams& mp, const float* z, const double* x) {
+        const int nb = (int)mp.p[3];
+        double s = 0.0;
+        for (int l = 0; l < nb; ++l) {
+            const float zl = z[l];
+            if (zl != zl) continue;
+            const double dx = x[0] - mp.p[4 + 2 * l], dy = x[1] - mp.p[5 + 2 * l];
+            const double res = (double)zl - sqrt(dx * dx + dy * dy);
+            s += -0.5 * res * res / mp.p[2] + mp.aux[0];
+        }
+        return s;
+    }
+};
+
 struct ModelRangeCV : CVTransition {
     static constexpr int KIND = 2, D = 4, DP = 4, DY = 8;
     __device__ static void grad_loglik(const ModelParams& mp, const float* z, const float* x, float* g) {
