@@ -48,7 +48,7 @@
 #define OM_MAXP 128
 
 enum { OM_NGM1D = 1, OM_RANGE_CV2D = 2, OM_CLUTTER_CV2D = 3, OM_PLANAR_ARM = 4,
-       OM_LINEAR_GAUSS = 5, OM_RANGE_ZV2D = 6 };
+       OM_LINEAR_GAUSS = 5, OM_RANGE_ZV2D = 6, OM_SE2_RB = 7 };
 enum { OM_BW_MEDIAN_ITER = 0, OM_BW_MEDIAN_STEP = 1, OM_BW_FIXED = 2 };
 enum { OM_PRIOR_MIXTURE = 0, OM_PRIOR_MEANGRAD = 1 };
 
@@ -78,6 +78,15 @@ typedef struct {
 /*  RANGE_ZV2D   [q0, q1, r, nb, b0x, b0y, ...]  state (px, py); zero-velocity */
 /*               random walk x_t = x_{t-1} + v (Section V-C's target model);  */
 /*               z_l = ||p - b_l|| + N(0, r); NaN = anchor not heard          */
+/*  SE2_RB       [dt, q0, q1, q2, rr, rb, v, omega, nl, L0x, L0y, ...]        */
+/*               pose (px, py, th) on SE(2) under constant controls (v, w)   */
+/*               (Section V-B's motion model): th' = th + w dt,              */
+/*               p' = p + v dt (cos th', sin th'); one range-bearing pair    */
+/*               z = (zr, zb) from ONE of nl landmarks, association unknown: */
+/*               p(z|x) = (1/nl) sum_l N(zr; rho_l, rr) N(wrap(zb - b_l); 0, rb) */
+/*               rho_l = ||p - L_l||, b_l = atan2(py - Lly, px - Llx);       */
+/*               wrap(a) = a - 2 pi n, n the nearest integer to a / (2 pi).  */
+/*               NaN zr = no measurement at that step.                       */
 /* ------------------------------------------------------------------------ */
 
 int om_setup(om_model* m, int kind, const double* p, int np)
@@ -129,6 +138,15 @@ int om_setup(om_model* m, int kind, const double* p, int np)
         m->q[0] = p[0]; m->q[1] = p[1];
         break;
     }
+    case OM_SE2_RB: {
+        if (np < 9) return -1;
+        int nl = (int)p[8];
+        if (nl < 1 || nl > 8 || np != 9 + 2 * nl) return -1;
+        if (!(p[4] > 0.0) || !(p[5] > 0.0)) return -1;
+        m->d = 3; m->dy = 2;
+        for (int k = 0; k < 3; ++k) m->q[k] = p[1 + k];
+        break;
+    }
     default:
         return -1;
     }
@@ -159,6 +177,13 @@ void om_transition(const om_model* m, int t, const double* x, double* f)
         f[0] = x[0];
         f[1] = x[1];
         break;
+    case OM_SE2_RB: {
+        double dt = p[0], th = x[2] + p[7] * dt;
+        f[0] = x[0] + p[6] * dt * cos(th);
+        f[1] = x[1] + p[6] * dt * sin(th);
+        f[2] = th;
+        break;
+    }
     case OM_PLANAR_ARM: {
         int nl = (int)p[1];
         double dt = p[0];
@@ -229,6 +254,24 @@ static void om_range_grad(const double* x, const double* z, int nb, double r, co
     }
 }
 
+/* Bearing residual brought to [-pi, pi]. */
+static double om_wrap(double a)
+{
+    return a - 2.0 * OM_PI * nearbyint(a / (2.0 * OM_PI));
+}
+
+/* log of the nl association terms of SE2_RB (each with its 1/nl weight). */
+static void om_se2_terms(const double* p, const double* z, const double* x, double* terms)
+{
+    int nl = (int)p[8];
+    for (int l = 0; l < nl; ++l) {
+        double dx = x[0] - p[9 + 2 * l], dy = x[1] - p[10 + 2 * l];
+        double rho = sqrt(dx * dx + dy * dy);
+        double eb = om_wrap(z[1] - atan2(dy, dx));
+        terms[l] = -log((double)nl) + om_lognorm1(z[0] - rho, p[4]) + om_lognorm1(eb, p[5]);
+    }
+}
+
 double om_loglik(const om_model* m, int t, const double* z, const double* x)
 {
     const double* p = m->p;
@@ -240,6 +283,15 @@ double om_loglik(const om_model* m, int t, const double* z, const double* x)
         return om_range_loglik(x, z, (int)p[6], p[5], p + 7);
     case OM_RANGE_ZV2D:
         return om_range_loglik(x, z, (int)p[3], p[2], p + 4);
+    case OM_SE2_RB: {
+        if (isnan(z[0])) return 0.0;
+        int nl = (int)p[8];
+        double terms[8], mx = -INFINITY, s = 0.0;
+        om_se2_terms(p, z, x, terms);
+        for (int l = 0; l < nl; ++l) if (terms[l] > mx) mx = terms[l];
+        for (int l = 0; l < nl; ++l) s += exp(terms[l] - mx);
+        return mx + log(s);
+    }
     case OM_CLUTTER_CV2D: {
         double r = p[5], beta = p[7], area = p[8];
         int M = (int)p[6];
@@ -286,6 +338,27 @@ void om_grad_loglik(const om_model* m, int t, const double* z, const double* x, 
     case OM_RANGE_ZV2D:
         om_range_grad(x, z, (int)p[3], p[2], p + 4, g);
         break;
+    case OM_SE2_RB: {
+        /* sum over landmarks of responsibility x gradient of that term;
+         * d b_l / d(px, py) = (-dy, dx) / rho^2 */
+        if (isnan(z[0])) break;
+        int nl = (int)p[8];
+        double terms[8];
+        double ll = om_loglik(m, t, z, x);
+        om_se2_terms(p, z, x, terms);
+        for (int l = 0; l < nl; ++l) {
+            double w = exp(terms[l] - ll);
+            double dx = x[0] - p[9 + 2 * l], dy = x[1] - p[10 + 2 * l];
+            double rho2 = dx * dx + dy * dy;
+            if (rho2 < 1e-18) rho2 = 1e-18;
+            double rho = sqrt(rho2);
+            double cr = (z[0] - rho) / p[4] / rho;
+            double cb = om_wrap(z[1] - atan2(dy, dx)) / p[5] / rho2;
+            g[0] += w * (cr * dx - cb * dy);
+            g[1] += w * (cr * dy + cb * dx);
+        }
+        break;
+    }
     case OM_CLUTTER_CV2D: {
         double r = p[5], beta = p[7], area = p[8];
         int M = (int)p[6];

@@ -25,13 +25,14 @@ def _random_case(oracle, kind, params, N, T, seed):
     return m, x0, hist, z
 
 
-@pytest.mark.parametrize("case", range(12))
+@pytest.mark.parametrize("case", range(15))
 def test_viterbi_equals_brute_force(oracle, case):
     """argmax over all N^T paths of J(s) (Theorem 1) equals the DP result."""
     kinds = [(1, W.ngm1d_params()), (5, W.linear_params(q=0.5, r=0.5)),
              (2, W.range_params(np.array([[0.0, 0.0], [3.0, 0.0], [0.0, 3.0]]), q=0.5, r=0.5)),
-             (6, W.zv_params(np.array([[0.0, 0.0], [3.0, 0.0], [0.0, 3.0]]), q=0.5, r=0.5))]
-    kind, params = kinds[case % 4]
+             (6, W.zv_params(np.array([[0.0, 0.0], [3.0, 0.0], [0.0, 3.0]]), q=0.5, r=0.5)),
+             (7, W.se2_params(np.array([[0.0, 0.0], [3.0, 0.0], [0.0, 3.0], [3.0, 3.0]]), alpha=(5, 5, 5)))]
+    kind, params = kinds[case % 5]
     N = 2 + case % 3
     T = 5 if N <= 3 else 4
     m, x0, hist, z = _random_case(oracle, kind, params, N, T, 100 + case)

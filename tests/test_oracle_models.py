@@ -28,6 +28,8 @@ def _models(O):
         "linear": (O.Model(5, W.linear_params()), lambda r: np.r_[r.normal(0, 3, 2), r.normal(0, 1, 2)],
                    lambda r: r.normal(0, 3, 2)),
         "range_zv": (O.Model(6, W.zv_params()), lambda r: r.uniform(-2, 12, 2), lambda r: r.uniform(0, 14, 3)),
+        "se2_rb": (O.Model(7, W.se2_params()), lambda r: np.r_[r.uniform(-11, 11, 2), r.uniform(-4, 4)],
+                   lambda r: np.r_[r.uniform(1, 25), r.uniform(-3, 3)]),
     }
 
 
@@ -103,6 +105,21 @@ def test_loglik_against_scipy(oracle):
         assert m.loglik(1, z, x) == pytest.approx(stats.norm.logpdf(z, rho, 0.5).sum(), rel=1e-12)
         z2 = z.copy(); z2[0] = np.nan
         assert m.loglik(1, z2, x) == pytest.approx(stats.norm.logpdf(z[1:], rho[1:], 0.5).sum(), rel=1e-12)
+    # SE2_RB: equal-weight mixture over the four landmarks of a range density
+    # times a bearing density of the residual taken on the circle
+    m = oracle.Model(7, W.se2_params())
+    lm = W.SE2_LANDMARKS
+    for _ in range(40):
+        x = np.r_[rng.uniform(-11, 11, 2), rng.uniform(-4, 4)]
+        z = np.r_[rng.uniform(1, 25), rng.uniform(-np.pi, np.pi)]
+        rho = np.linalg.norm(x[:2] - lm, axis=1)
+        bear = np.arctan2(x[1] - lm[:, 1], x[0] - lm[:, 0])
+        res = np.angle(np.exp(1j * (z[1] - bear)))
+        ref = special.logsumexp(stats.norm.logpdf(z[0], rho, 1.0) + stats.norm.logpdf(res, 0, 0.44)) - np.log(4)
+        assert m.loglik(1, z, x) == pytest.approx(ref, rel=1e-12)
+        # the heading does not enter the measurement
+        assert m.loglik(1, z, np.r_[x[:2], x[2] + 1.0]) == pytest.approx(ref, rel=1e-12)
+    assert m.loglik(1, np.array([np.nan, 0.3]), np.zeros(3)) == 0.0
     # LINEAR_GAUSS
     m = oracle.Model(5, W.linear_params())
     x = rng.normal(0, 1, 4); z = rng.normal(0, 1, 2)
@@ -128,6 +145,31 @@ def test_logtrans_and_transition_against_scipy(oracle):
     assert np.array_equal(m.transition(7, x), x)
     f = rng.normal(0, 3, 2)
     assert m.logtrans(x, f) == pytest.approx(stats.multivariate_normal.logpdf(x, f, 0.01 * np.eye(2)), rel=1e-12)
+    # SE(2) motion with constant controls: K steps of heading increment
+    # 2 pi / K trace a closed regular K-gon, counter-clockwise for w > 0, whose
+    # vertices lie on a circle of radius v dt / (2 sin(pi / K))
+    K, dt, v = 100, 0.1, 1.0
+    w = 2 * np.pi / K / dt
+    p = W.se2_params(v=v, w=w, dt=dt)
+    m = oracle.Model(7, p)
+    x = np.array([3.0, -1.0, 0.4])
+    pts = [x]
+    for t in range(K):
+        pts.append(m.transition(t + 1, pts[-1]))
+    pts = np.array(pts)
+    assert np.allclose(pts[-1, :2], pts[0, :2], atol=1e-12)
+    assert pts[-1, 2] == pytest.approx(pts[0, 2] + 2 * np.pi, abs=1e-12)
+    # Section V-B moves the position along the NEW heading theta_t
+    step1 = pts[1, :2] - pts[0, :2]
+    assert np.arctan2(step1[1], step1[0]) == pytest.approx(0.4 + w * dt, abs=1e-12)
+    side = np.linalg.norm(np.diff(pts[:, :2], axis=0), axis=1)
+    assert np.allclose(side, v * dt, rtol=1e-12)
+    xy = pts[:-1, :2]
+    area = 0.5 * np.sum(xy[:, 0] * np.roll(xy[:, 1], -1) - np.roll(xy[:, 0], -1) * xy[:, 1])
+    R = v * dt / (2 * np.sin(np.pi / K))
+    assert area == pytest.approx(0.5 * K * R * R * np.sin(2 * np.pi / K), rel=1e-9)
+    centre = xy.mean(axis=0)
+    assert np.allclose(np.linalg.norm(xy - centre, axis=1), R, rtol=1e-9)
     # NGM1D time dependence: cos(1.2 t) in the workload form, cos(1.2 (t-1)) in the paper's
     m = oracle.Model(1, W.ngm1d_params())
     assert m.transition(3, [2.0])[0] == pytest.approx(1.0 + 50.0 / 5.0 + 8 * np.cos(3.6), rel=1e-14)
@@ -135,7 +177,8 @@ def test_logtrans_and_transition_against_scipy(oracle):
     assert m.transition(3, [2.0])[0] == pytest.approx(1.8 + 20.0 / 5.0 + 8 * np.cos(2.4), rel=1e-14)
 
 
-@pytest.mark.parametrize("name", ["ngm1d", "ngm1d_paper", "range", "clutter", "arm", "linear", "range_zv"])
+@pytest.mark.parametrize("name", ["ngm1d", "ngm1d_paper", "range", "clutter", "arm", "linear", "range_zv",
+                                  "se2_rb"])
 def test_grad_loglik_finite_differences(oracle, name):
     m, xs, zs = _models(oracle)[name]
     rng = np.random.default_rng(3)
