@@ -70,6 +70,13 @@ typedef enum {
  *      state (px, py) without a motion prior: x_t = x_{t-1} + N(0, diag(q0, q1));
  *      z_l = ||x - a_l|| + N(0, r), NaN = anchor l not heard (Section V-C's
  *      zero-velocity model)
+ *  SMAP_MODEL_SE2_RB       [dt, q0, q1, q2, rr, rb, v, w, nl, L0x, L0y, ...] d=3, dy=2 (nl 1..8)
+ *      pose (px, py, th) on SE(2) under constant controls: th' = th + w dt,
+ *      (px, py)' = (px, py) + v dt (cos th', sin th') + N(0, diag(q0..q2));
+ *      z = (range, bearing) from one of nl landmarks, association unknown:
+ *      p(z|x) = (1/nl) sum_l N(zr; ||p - L_l||, rr) N(wrap(zb - b_l); 0, rb),
+ *      b_l = atan2(py - L_ly, px - L_lx), wrap into [-pi, pi]; a NaN range means
+ *      no measurement at that step (Section V-B's model)
  */
 typedef enum {
     SMAP_MODEL_NGM1D = 1,
@@ -77,7 +84,8 @@ typedef enum {
     SMAP_MODEL_CLUTTER_CV2D = 3,
     SMAP_MODEL_PLANAR_ARM = 4,
     SMAP_MODEL_LINEAR_GAUSS = 5,
-    SMAP_MODEL_RANGE_ZV2D = 6
+    SMAP_MODEL_RANGE_ZV2D = 6,
+    SMAP_MODEL_SE2_RB = 7
 } smap_model;
 
 /* Kernel bandwidth h of kappa(x,x') = exp(-||x-x'||^2 / h) (the RBF kernel of

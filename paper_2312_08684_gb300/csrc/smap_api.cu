@@ -90,7 +90,7 @@ __global__ void normals_kernel(uint64_t seed, uint32_t seq, uint32_t t, uint32_t
 }
 
 const ModelKernels* kernels_for(int kind) {
-    static ModelKernels tab[7];
+    static ModelKernels tab[8];
     static bool init = false;
     if (!init) {
         tab[1] = kernels_ngm1d();
@@ -99,9 +99,10 @@ const ModelKernels* kernels_for(int kind) {
         tab[4] = kernels_planar_arm7();
         tab[5] = kernels_linear_gauss();
         tab[6] = kernels_range_zv();
+        tab[7] = kernels_se2_rb();
         init = true;
     }
-    if (kind < 1 || kind > 6) return nullptr;
+    if (kind < 1 || kind > 7) return nullptr;
     return &tab[kind];
 }
 
@@ -159,6 +160,20 @@ bool make_model(int kind, const double* p, int np, ModelParams& mp, std::string&
         mp.d = 2; mp.dy = nb;
         mp.q[0] = p[0]; mp.q[1] = p[1];
         mp.aux[0] = -0.5 * std::log(two_pi * p[2]); mp.auxf[0] = (float)(1.0 / p[2]);
+        break;
+    }
+    case SMAP_MODEL_SE2_RB: {
+        const int nl = np >= 9 ? (int)p[8] : 0;
+        if (nl < 1 || nl > 8 || np != 9 + 2 * nl) { err = "SE2_RB: expects 9 + 2 nl parameters, nl 1..8"; return false; }
+        if (!(p[4] > 0) || !(p[5] > 0)) { err = "SE2_RB: rr and rb must be > 0"; return false; }
+        if (!std::isfinite(p[0]) || !std::isfinite(p[6]) || !std::isfinite(p[7])) { err = "SE2_RB: dt, v, w must be finite"; return false; }
+        mp.d = 3; mp.dy = 2;
+        for (int c = 0; c < 3; ++c) mp.q[c] = p[1 + c];
+        const double log2e = 1.4426950408889634;
+        mp.aux[0] = -std::log((double)nl) - 0.5 * std::log(two_pi * p[4]) - 0.5 * std::log(two_pi * p[5]);
+        mp.auxf[0] = (float)(p[6] * p[0]); mp.auxf[1] = (float)(p[7] * p[0]);
+        mp.auxf[2] = (float)(-0.5 * log2e / p[4]); mp.auxf[3] = (float)(-0.5 * log2e / p[5]);
+        mp.auxf[4] = (float)(1.0 / p[4]); mp.auxf[5] = (float)(1.0 / p[5]);
         break;
     }
     case SMAP_MODEL_LINEAR_GAUSS:

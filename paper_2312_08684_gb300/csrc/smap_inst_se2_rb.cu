@@ -1,0 +1,24 @@
+// Step-kernel instantiations for ModelSE2RB.
+#include "smap_internal.h"
+#include "smap_kernels.cuh"
+
+namespace smap {
+
+ModelKernels kernels_se2_rb() {
+    using M = ModelSE2RB;
+    ModelKernels k;
+    k.kind = M::KIND;
+    k.D = M::D;
+    k.DP = M::DP;
+    k.seq[0] = (const void*)seq_kernel<M, 1, 1024, 1>;
+    k.seq[1] = (const void*)seq_kernel<M, 2, 512, 1>;
+    k.seq[2] = (const void*)seq_kernel<M, 4, 256, 1>;
+    k.seq[3] = (const void*)seq_kernel<M, 2, 256, 4>;
+    k.dbg[0] = (const void*)debug_svgd_kernel<M, 1, 1024, 1>;
+    k.dbg[1] = (const void*)debug_svgd_kernel<M, 2, 512, 1>;
+    k.dbg[2] = (const void*)debug_svgd_kernel<M, 4, 256, 1>;
+    k.dbg[3] = (const void*)debug_svgd_kernel<M, 2, 256, 4>;
+    return k;
+}
+
+}  // namespace smap

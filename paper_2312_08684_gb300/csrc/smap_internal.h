@@ -29,6 +29,7 @@ ModelKernels kernels_clutter_cv();
 ModelKernels kernels_planar_arm7();
 ModelKernels kernels_linear_gauss();
 ModelKernels kernels_range_zv();
+ModelKernels kernels_se2_rb();
 
 // Rows of the learned proposal: propagated particles u = f_t(x_{t-1}^i) + noise
 // (drawn exactly like the step kernels' initialisation) and their features.

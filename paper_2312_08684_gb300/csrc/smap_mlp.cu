@@ -459,6 +459,7 @@ const void* proposal_rows_fn(int kind) {
     case 4: return (const void*)proposal_rows_kernel<ModelPlanarArm<7>>;
     case 5: return (const void*)proposal_rows_kernel<ModelLinearGauss>;
     case 6: return (const void*)proposal_rows_kernel<ModelRangeZV>;
+    case 7: return (const void*)proposal_rows_kernel<ModelSE2RB>;
     }
     return nullptr;
 }

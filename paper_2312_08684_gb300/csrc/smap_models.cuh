@@ -59,11 +59,10 @@ struct CVTransition {
     }
 };
 
-// Range-only localisation. p = [dt, q0..q3, r, nb, b0x, b0y, ...].
-// aux[0] = -1/2 log(2 pi r), auxf[0] = 1/r. NaN observation = beacon not heard.
 // Section V-C's target without a motion prior: x = (px, py), zero-velocity
 // random walk x_t = x_{t-1} + v; ranges to nb anchors. Parameters
 // [q0, q1, r, nb, a0x, a0y, ...]; NaN = anchor not heard.
+// aux[0] = -1/2 log(2 pi r), auxf[0] = 1/r.
 struct ModelRangeZV {
     static constexpr int KIND = 6, D = 2, DP = 2, DY = 8;
     __device__ static double step_const(const ModelParams&, int) { return 0.0; }
@@ -103,6 +102,91 @@ struct ModelRangeZV {
     }
 };
 
+// Section V-B's pose on SE(2) under unknown association: x = (px, py, th),
+// constant controls (v, w): th' = th + w dt, p' = p + v dt (cos th', sin th').
+// One measurement z = (zr, zb) per step from one of nl landmarks, association
+// marginalised with weights 1/nl:
+//   p(z | x) = (1/nl) sum_l N(zr; rho_l, rr) N(wrap(zb - b_l); 0, rb),
+//   rho_l = |p - L_l|, b_l = atan2(py - L_ly, px - L_lx), wrap into [-pi, pi].
+// p = [dt, q0, q1, q2, rr, rb, v, w, nl, L0x, L0y, ...]; NaN zr = no measurement.
+// aux[0] = -log nl - 1/2 log(2 pi rr) - 1/2 log(2 pi rb);
+// auxf[0] = v dt, auxf[1] = w dt, auxf[2] = -log2(e) / (2 rr), auxf[3] = -log2(e) / (2 rb),
+// auxf[4] = 1/rr, auxf[5] = 1/rb.
+struct ModelSE2RB {
+    static constexpr int KIND = 7, D = 3, DP = 4, DY = 2;
+    __device__ static double step_const(const ModelParams&, int) { return 0.0; }
+    __device__ static void transition(const ModelParams& mp, double, const float* x, float* f) {
+        const float th = x[2] + mp.auxf[1];
+        float sn, cs;
+        sincosf(th, &sn, &cs);
+        f[0] = fmaf(mp.auxf[0], cs, x[0]);
+        f[1] = fmaf(mp.auxf[0], sn, x[1]);
+        f[2] = th;
+    }
+    __device__ static void transition64(const ModelParams& mp, double, const double* x, double* f) {
+        const double dt = mp.p[0], th = x[2] + mp.p[7] * dt;
+        f[0] = x[0] + mp.p[6] * dt * cos(th);
+        f[1] = x[1] + mp.p[6] * dt * sin(th);
+        f[2] = th;
+    }
+    __device__ static float wrapf(float a) {
+        return fmaf(-6.2831853071795865f, rintf(a * 0.15915494309189535f), a);
+    }
+    __device__ static void grad_loglik(const ModelParams& mp, const float* z, const float* x, float* g) {
+        g[0] = 0.0f; g[1] = 0.0f; g[2] = 0.0f;
+        if (z[0] != z[0]) return;
+        const int nl = (int)mp.p[8];
+        // log2 of each association term (shared constants dropped), then
+        // responsibilities by a max-shifted sum
+        float lt[8], cr[8], cb[8], ddx[8], ddy[8];
+        float mx = -INFINITY;
+#pragma unroll
+        for (int l = 0; l < 8; ++l) {
+            if (l >= nl) break;
+            const float dx = x[0] - mp.pf[9 + 2 * l], dy = x[1] - mp.pf[10 + 2 * l];
+            const float rho2 = fmaxf(fmaf(dx, dx, dy * dy), 1e-18f);
+            const float rho = sqrtf(rho2);
+            const float er = z[0] - rho;
+            const float eb = wrapf(z[1] - atan2f(dy, dx));
+            lt[l] = fmaf(mp.auxf[2], er * er, mp.auxf[3] * eb * eb);
+            cr[l] = er * mp.auxf[4] / rho;
+            cb[l] = eb * mp.auxf[5] / rho2;
+            ddx[l] = dx; ddy[l] = dy;
+            mx = fmaxf(mx, lt[l]);
+        }
+        float s = 0.0f, g0 = 0.0f, g1 = 0.0f;
+#pragma unroll
+        for (int l = 0; l < 8; ++l) {
+            if (l >= nl) break;
+            const float w = fast_exp2(lt[l] - mx);
+            s += w;
+            g0 = fmaf(w, fmaf(cr[l], ddx[l], -cb[l] * ddy[l]), g0);
+            g1 = fmaf(w, fmaf(cr[l], ddy[l], cb[l] * ddx[l]), g1);
+        }
+        const float k = 1.0f / s;
+        g[0] = g0 * k; g[1] = g1 * k;
+    }
+    __device__ static double loglik64(const ModelParams& mp, const float* z, const double* x) {
+        if (z[0] != z[0]) return 0.0;
+        const int nl = (int)mp.p[8];
+        const double zr = z[0], zb = z[1];
+        double lt[8], mx = -INFINITY;
+        for (int l = 0; l < nl; ++l) {
+            const double dx = x[0] - mp.p[9 + 2 * l], dy = x[1] - mp.p[10 + 2 * l];
+            const double er = zr - sqrt(dx * dx + dy * dy);
+            double eb = zb - atan2(dy, dx);
+            eb -= 6.283185307179586 * rint(eb / 6.283185307179586);
+            lt[l] = -0.5 * (er * er / mp.p[4] + eb * eb / mp.p[5]);
+            mx = fmax(mx, lt[l]);
+        }
+        double s = 0.0;
+        for (int l = 0; l < nl; ++l) s += exp(lt[l] - mx);
+        return mp.aux[0] + mx + log(s);
+    }
+};
+
+// Range-only localisation. p = [dt, q0..q3, r, nb, b0x, b0y, ...].
+// aux[0] = -1/2 log(2 pi r), auxf[0] = 1/r. NaN observation = beacon not heard.
 struct ModelRangeCV : CVTransition {
     static constexpr int KIND = 2, D = 4, DP = 4, DY = 8;
     __device__ static void grad_loglik(const ModelParams& mp, const float* z, const float* x, float* g) {

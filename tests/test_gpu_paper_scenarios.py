@@ -93,3 +93,42 @@ def test_range_only_rmse_stays_bounded_through_blocking(N):
     print(f"N={N}: MAP-sequence position RMSE per run {np.round(rmse, 3)}")
     assert np.all(np.isfinite(J))
     assert float(np.mean(rmse)) < 0.5
+
+
+# --------------------------------------------- Section V-B (SE(2), unknown association) --
+def test_se2_range_bearing_matches_oracle(oracle):
+    """SE(2) pose with constant controls, one range-bearing measurement per
+    step from one of four landmarks (association marginalised), 10% outliers
+    at four times the noise scale; Q, noise levels and 100 iterations as in
+    Section V-B, SVGD step 1e-4 (see make_se2_rb). GPU vs oracle on a short run."""
+    wl = W.make_se2_rb(B=2, T=40, N=20)
+    with Estimator.from_workload(wl) as est:
+        path, J = est.run_batch(wl.y)
+    for b in range(wl.B):
+        ref = oracle.run_sequence(wl.kind, wl.params, wl.N, wl.L, wl.step, wl.bw_rule, wl.bw_value, wl.prior,
+                                  wl.seed, b, wl.x0[b], wl.y[b].astype(np.float64))
+        assert _rel_err(path[b], ref["path"]) <= 1e-3
+        assert J[b] == pytest.approx(ref["J"], rel=1e-3)
+
+
+def test_se2_map_sequence_beats_the_true_trajectory_in_J(oracle):
+    """Ten 630-step runs (the paper's Monte Carlo size): the MAP sequence over
+    the particle supports must score at least as high as the simulated truth
+    under the same model (J of Theorem 1, the truth's J from the oracle), and
+    track the truth better than dead reckoning with the known controls."""
+    wl = W.make_se2_rb(B=10, T=630, N=20)
+    with Estimator.from_workload(wl) as est:
+        path, J = est.run_batch(wl.y)
+    m = oracle.Model(wl.kind, wl.params)
+    rm, rd = [], []
+    for b in range(wl.B):
+        Jt = m.path_score(wl.truth[b], wl.y[b].astype(np.float64))
+        assert J[b] >= Jt, (b, J[b], Jt)
+        dr = [wl.x0[b]]
+        for t in range(wl.maxT):
+            dr.append(m.transition(t + 1, dr[-1]))
+        dr = np.array(dr)
+        rm.append(np.sqrt(np.mean(np.sum((path[b, 1:, :2] - wl.truth[b, 1:, :2]) ** 2, axis=1))))
+        rd.append(np.sqrt(np.mean(np.sum((dr[1:, :2] - wl.truth[b, 1:, :2]) ** 2, axis=1))))
+    print(f"SE(2): MAP-sequence position RMSE {np.mean(rm):.3f} m, dead reckoning {np.mean(rd):.3f} m")
+    assert np.mean(rm) < np.mean(rd)

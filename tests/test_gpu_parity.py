@@ -58,8 +58,9 @@ CASES = {
     "arm": lambda: W.make_planar_arm(B=2, T=6, N=33, L=1),
     "linear": lambda: W.make_linear_gauss(B=2, T=6, N=29, L=1),
     "range_zv": lambda: W.make_range_zv(B=2, T=6, N=41, L=1, blocked=((2, 2),)),
+    "se2": lambda: W.make_se2_rb(B=2, T=6, N=43, L=1, step=5e-4),
 }
-SPREAD = {"ngm1d": 2.0, "range": 0.3, "clutter": 0.3, "arm": 0.02, "linear": 0.2, "range_zv": 0.2}
+SPREAD = {"ngm1d": 2.0, "range": 0.3, "clutter": 0.3, "arm": 0.02, "linear": 0.2, "range_zv": 0.2, "se2": 0.1}
 
 
 def _svgd_case(oracle, name, t, n_iters, prior=0, bw_rule=0, bw_value=1.0, N=None, kernel=0):
@@ -121,7 +122,7 @@ def test_particle_counts_edge_cases(oracle, N):
 
 
 @pytest.mark.parametrize("kernel", [1, 2])
-@pytest.mark.parametrize("name", ["ngm1d", "range", "clutter", "arm", "range_zv"])
+@pytest.mark.parametrize("name", ["ngm1d", "range", "clutter", "arm", "range_zv", "se2"])
 def test_ablation_kernels_match_oracle(oracle, name, kernel):
     """IMQ and Matern 3/2 Stein kernels (Table Ex6's alternatives): one
     iteration at t = 1 and t = 3, GPU vs oracle."""
@@ -156,13 +157,14 @@ def _margins(m, x0, hist, z):
     return out
 
 
-@pytest.mark.parametrize("name", ["ngm1d", "range", "clutter", "arm", "range_zv"])
+@pytest.mark.parametrize("name", ["ngm1d", "range", "clutter", "arm", "range_zv", "se2"])
 def test_viterbi_on_identical_particle_sets(oracle, name):
     wl = {"ngm1d": lambda: W.make_ngm1d(B=2, T=9, N=19),
           "range": lambda: W.make_range_cv(B=2, T=9, N=35, dropout=(3, 5)),
           "clutter": lambda: W.make_clutter_cv(B=2, Tmin=9, Tmax=9, N=40),
           "arm": lambda: W.make_planar_arm(B=2, T=9, N=24),
-          "range_zv": lambda: W.make_range_zv(B=2, T=9, N=30, blocked=((3, 3),))}[name]()
+          "range_zv": lambda: W.make_range_zv(B=2, T=9, N=30, blocked=((3, 3),)),
+          "se2": lambda: W.make_se2_rb(B=2, T=9, N=28)}[name]()
     m = oracle.Model(wl.kind, wl.params)
     rng = np.random.default_rng(5)
     B, T, N, d = wl.B, wl.maxT, wl.N, wl.d
@@ -203,12 +205,13 @@ def test_full_run_ngm1d_matches_oracle(oracle):
     assert J[0] == pytest.approx(ref["J"], rel=1e-3)
 
 
-@pytest.mark.parametrize("name", ["range", "clutter", "linear", "range_zv"])
+@pytest.mark.parametrize("name", ["range", "clutter", "linear", "range_zv", "se2"])
 def test_full_run_small_matches_oracle(oracle, name):
     wl = {"range": lambda: W.make_range_cv(B=3, T=25, N=64, L=10, dropout=(8, 14)),
           "clutter": lambda: W.make_clutter_cv(B=3, Tmin=10, Tmax=20, N=48, L=10),
           "linear": lambda: W.make_linear_gauss(B=3, T=15, N=40, L=20),
-          "range_zv": lambda: W.make_range_zv(B=3, T=30, N=40, L=20, blocked=((8, 10),))}[name]()
+          "range_zv": lambda: W.make_range_zv(B=3, T=30, N=40, L=20, blocked=((8, 10),)),
+          "se2": lambda: W.make_se2_rb(B=3, T=30, N=40, L=20)}[name]()
     path, J, hist, psi = _run_gpu(wl)
     for b in range(wl.B):
         T = int(wl.T[b])
