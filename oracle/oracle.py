@@ -101,6 +101,10 @@ def lib():
                                           _D, _D, _I, _D, _D]
             L.om_viterbi_sets.argtypes = [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           _D, _D, _D, _I, _D, _D, _D]
+            L.om_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
+            L.om_uniform.restype = ctypes.c_double
+            L.om_pf_sets.argtypes = [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                     ctypes.c_uint32, _D, _D, _D, _I]
             L.om_viterbi_margins.argtypes = [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              _D, _D, _D, _D]
             L.om_mlp_nparams.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -268,6 +272,36 @@ def viterbi_sets(kind, params, x0, hist, z):
     if rc != 0:
         raise ValueError("oracle: viterbi_sets rejected its input")
     return {"psi": psi, "phiT": phiT, "path": path, "J": J.value}
+
+
+def uniform(seed, seq, t, i):
+    """U_i of the stratified resampling: (w0 + 1/2) / 2^32, Philox counter (i, t, seq, 256)."""
+    return lib().om_uniform(ctypes.c_uint64(seed), seq, t, i)
+
+
+def pf_sets(kind, params, N, seed, seq, x0, z):
+    """Bootstrap particle filter with stratified resampling at every step (the
+    supports of PF-MAP-Seq): hist [T][N][d] and ancestors [T][N]."""
+    m = Model(kind, params)
+    z = _f64(z).reshape(-1, m.dy).copy()
+    T = z.shape[0]
+    x0 = _f64(x0)
+    hist = np.empty((T, N, m.d)); anc = np.empty((T, N), dtype=np.int32)
+    rc = lib().om_pf_sets(m.kind, _dp(m.params), len(m.params), N, T, ctypes.c_uint64(seed), seq, _dp(x0),
+                          _dp(z), _dp(hist), _ip(anc))
+    if rc != 0:
+        raise ValueError("oracle: pf_sets rejected its input")
+    return hist, anc
+
+
+def pf_map_sequence(kind, params, N, seed, seq, x0, z):
+    """PF-MAP-Seq: the particle filter's sets, then the forward recursion and
+    backtracking over them."""
+    hist, anc = pf_sets(kind, params, N, seed, seq, x0, z)
+    res = viterbi_sets(kind, params, x0, hist, z)
+    res["hist"] = hist
+    res["anc"] = anc
+    return res
 
 
 def viterbi_margins(kind, params, x0, hist, z):

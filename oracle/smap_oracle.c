@@ -744,6 +744,71 @@ int om_viterbi_sets(int kind, const double* params, int np, int N, int T,
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* PF-MAP-Seq, the comparison method of Section V (Godsill, Doucet and West, */
+/* "Maximum a posteriori sequence estimation using Monte Carlo particle      */
+/* filters", 2001): a bootstrap particle filter supplies the supports, the   */
+/* same forward recursion and backtracking then pick the MAP sequence.       */
+/* Readings (the paper names the method and its stratified resampling at     */
+/* every step, nothing more):                                                */
+/*   x_1^i = f_1(x_0) + sqrt(q) (.) xi, log w_1^i = log p(z_1 | x_1^i);       */
+/*   t >= 2: stratified resampling of the step t-1 weights, u_i = (i + U_i)/N,*/
+/*   ancestor a_i = the first j whose normalised cumulative weight exceeds   */
+/*   u_i; x_t^i = f_t(x_{t-1}^{a_i}) + sqrt(q) (.) xi; log w_t^i =            */
+/*   log p(z_t | x_t^i). xi: om_normals with counter (i, t, seq, block);      */
+/*   U_i = (w0 + 1/2) / 2^32 from the Philox word w0 of counter               */
+/*   (i, t, seq, 256). The supports of the recursion are the sets x_t.       */
+/* ------------------------------------------------------------------------ */
+double om_uniform(uint64_t seed, uint32_t seq, uint32_t t, uint32_t i)
+{
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t ctr[4] = { i, t, seq, 256u }, w[4];
+    om_philox4x32_10(ctr, key, w);
+    return ((double)w[0] + 0.5) * (1.0 / 4294967296.0);
+}
+
+/* hist [T][N][d] (out), anc [T][N] ancestors (out, anc[0][i] = 0; may be NULL). */
+int om_pf_sets(int kind, const double* params, int np, int N, int T, uint64_t seed, uint32_t seq,
+               const double* x0, const double* z, double* hist, int* anc)
+{
+    om_model m;
+    if (om_setup(&m, kind, params, np) || N < 1 || T < 1) return -1;
+    int d = m.d;
+    double* lw = (double*)malloc(sizeof(double) * N);
+    double* c = (double*)malloc(sizeof(double) * N);
+    double f[OM_MAXD], xi[OM_MAXD];
+    for (int t = 1; t <= T; ++t) {
+        double* cur = hist + (size_t)(t - 1) * N * d;
+        const double* prev = t > 1 ? hist + (size_t)(t - 2) * N * d : NULL;
+        if (t > 1) {
+            /* normalised cumulative weights of step t-1 */
+            double mx = -INFINITY, W = 0.0;
+            for (int j = 0; j < N; ++j) if (lw[j] > mx) mx = lw[j];
+            for (int j = 0; j < N; ++j) { W += exp(lw[j] - mx); c[j] = W; }
+            for (int j = 0; j < N; ++j) c[j] /= W;
+            for (int i = 0; i < N; ++i) {
+                double u = ((double)i + om_uniform(seed, seq, (uint32_t)t, (uint32_t)i)) / (double)N;
+                int a = 0;
+                while (a < N - 1 && !(c[a] > u)) ++a;
+                if (anc) anc[(size_t)(t - 1) * N + i] = a;
+                om_transition(&m, t, prev + (size_t)a * d, f);
+                om_normals(seed, seq, (uint32_t)t, (uint32_t)i, d, xi);
+                for (int k = 0; k < d; ++k) cur[(size_t)i * d + k] = f[k] + sqrt(m.q[k]) * xi[k];
+            }
+        } else {
+            om_transition(&m, 1, x0, f);
+            for (int i = 0; i < N; ++i) {
+                if (anc) anc[i] = 0;
+                om_normals(seed, seq, 1u, (uint32_t)i, d, xi);
+                for (int k = 0; k < d; ++k) cur[(size_t)i * d + k] = f[k] + sqrt(m.q[k]) * xi[k];
+            }
+        }
+        for (int i = 0; i < N; ++i) lw[i] = om_loglik(&m, t, z + (size_t)(t - 1) * m.dy, cur + (size_t)i * d);
+    }
+    free(lw); free(c);
+    return 0;
+}
+
 /* For fixed particle sets: the relative margin of every backpointer,
  * (best - second best) / max(1, |best|) over j of phi_{t-1}(j) +
  * log p(x_t^i | x_{t-1}^j), margin[T][N] (t = 1 has a single candidate:
