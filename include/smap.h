@@ -189,6 +189,26 @@ smap_status smap_viterbi(smap_handle* h, const float* hist, const float* y_all,
                          const int* T_per_seq, const int* N_per_seq, float* path,
                          double* J, uint16_t* psi, int on_device);
 
+/* PF-MAP-Seq, the particle-filter comparison method of Section V (Godsill,
+ * Doucet and West 2001): for every sequence a bootstrap particle filter with
+ * stratified resampling at every step supplies the supports, then the same
+ * forward recursion and backtracking as Stein-MAP-Seq give the MAP sequence
+ * over them. Per step t: x_1^i = f_1(x_0) + sqrt(q) (.) xi_i; for t >= 2 the
+ * step t-1 weights w_j = p(z_{t-1} | x_{t-1}^j) are normalised and summed,
+ * u_i = (i + U_i) / N, ancestor a_i = the first j whose cumulative weight
+ * exceeds u_i, x_t^i = f_t(x_{t-1}^{a_i}) + sqrt(q) (.) xi_i. xi and U come
+ * from Philox-4x32-10 keyed by smap_config.seed (counters (i, t, seq, block)
+ * and (i, t, seq, 256)); the filter runs in FP64, the recursion on FP32 copies.
+ * Uses the handle's model, N (up to 4096), B, max_T and seed; L, step, the
+ * bandwidth, prior, kernel and any attached proposal are ignored. y_all,
+ * T_per_seq, N_per_seq, path, J as in smap_run_batch; afterwards the handle
+ * holds the filter's particle sets as its history (smap_get_history) and the
+ * backpointers (smap_get_backpointers). The first call allocates 8 B N (d + 1)
+ * bytes of device memory per sequence (SMAP_E_NOMEM if that fails).
+ * Synchronises the stream. */
+smap_status smap_pf_run_batch(smap_handle* h, const float* y_all, const int* T_per_seq,
+                              const int* N_per_seq, float* path, double* J, int on_device);
+
 /* smap_viterbi for callers that cannot allocate device memory. (The paper has
  * no counterpart; it exists for the library's callers.) Some callers cannot
  * call cudaMalloc: a plug-in whose host application owns the device-memory

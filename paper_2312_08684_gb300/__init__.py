@@ -59,6 +59,14 @@ class Estimator:
         abi.smap_run_batch(self.h, y_all, T, Nseq, path, J)
         return path, J
 
+    def pf_run_batch(self, y_all, T=None, Nseq=None, path=None, J=None):
+        """PF-MAP-Seq over the batch: bootstrap-filter supports, same recursion."""
+        if path is None:
+            path = np.empty((self.B, self.max_T + 1, self.d), np.float32)
+            J = np.empty(self.B, np.float64)
+        abi.smap_pf_run_batch(self.h, y_all, T, Nseq, path, J)
+        return path, J
+
     def step(self, y, active=None):
         abi.smap_step(self.h, y, active)
 

@@ -34,7 +34,7 @@ EXPORTS = [
     "smap_proposal_create", "smap_proposal_destroy", "smap_proposal_dims", "smap_proposal_get_weights",
     "smap_proposal_set_weights", "smap_proposal_fit_normalization", "smap_proposal_forward",
     "smap_proposal_loss_grad", "smap_proposal_train", "smap_proposal_last_error", "smap_proposal_capture",
-    "smap_set_proposal",
+    "smap_set_proposal", "smap_pf_run_batch",
 ]
 MLP_IN_P, MLP_OUT_P, MLP_H = 32, 16, 256
 
@@ -80,6 +80,7 @@ def load():
     L.smap_step.argtypes = [_VP, _VP, _VP, _I]
     L.smap_map_sequence.argtypes = [_VP, _VP, _VP, _I]
     L.smap_run_batch.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _I]
+    L.smap_pf_run_batch.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _I]
     L.smap_get_history.argtypes = [_VP, _VP, _I]
     L.smap_get_backpointers.argtypes = [_VP, _VP, _I]
     L.smap_get_scores.argtypes = [_VP, _VP, _I]
@@ -229,6 +230,15 @@ def smap_run_batch(h, y_all, T_per_seq=None, N_per_seq=None, path=None, J=None):
     pp, d3, k3 = _arg(path, np.float32, True)
     pj, d4, k4 = _arg(J, np.float64, True)
     _check(load().smap_run_batch(h, py, pt, pn, pp, pj, _same_side(d0, d3, d4)), h)
+
+
+def smap_pf_run_batch(h, y_all, T_per_seq=None, N_per_seq=None, path=None, J=None):
+    py, d0, k0 = _arg(y_all, np.float32)
+    pt, _, k1 = _arg(None if T_per_seq is None else np.asarray(T_per_seq, np.int32), np.int32)
+    pn, _, k2 = _arg(None if N_per_seq is None else np.asarray(N_per_seq, np.int32), np.int32)
+    pp, d3, k3 = _arg(path, np.float32, True)
+    pj, d4, k4 = _arg(J, np.float64, True)
+    _check(load().smap_pf_run_batch(h, py, pt, pn, pp, pj, _same_side(d0, d3, d4)), h)
 
 
 def smap_get_history(h, out):

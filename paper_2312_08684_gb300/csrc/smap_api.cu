@@ -13,6 +13,7 @@
 #include "smap.h"
 #include "smap_internal.h"
 #include "smap_kernels.cuh"
+#include "smap_pf.cuh"
 
 using namespace smap;
 
@@ -271,6 +272,9 @@ struct smap_handle {
     float* lu = nullptr;       // [B][Nmax][d]
     float* lxinit = nullptr;   // [B][Nmax][d]
     cudaStream_t side = nullptr;   // second chain of the learned launches
+    // PF-MAP-Seq state (allocated by the first smap_pf_run_batch)
+    double* pf_x64 = nullptr;  // [B][Nmax][d]
+    double* pf_lw = nullptr;   // [B][Nmax]
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 };
 
@@ -638,7 +642,7 @@ void smap_destroy(smap_handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->step_done) cudaEventDestroy(h->step_done);
-    for (void* q : {(void*)h->lfeat, (void*)h->lu, (void*)h->lxinit})
+    for (void* q : {(void*)h->lfeat, (void*)h->lu, (void*)h->lxinit, (void*)h->pf_x64, (void*)h->pf_lw})
         if (q) cudaFree(q);
     if (h->side) cudaStreamDestroy(h->side);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
@@ -952,6 +956,70 @@ smap_status smap_viterbi(smap_handle* h, const float* hist, const float* y_all, 
     if (psi)
         SMAP_CUDA(h, cudaMemcpyAsync(psi, h->psi, sizeof(uint16_t) * (size_t)h->B * h->maxT * h->Nmax,
                                      kind_out(on_device), h->stream));
+    st = copy_outputs(h, path, J, on_device);
+    if (st) return st;
+    return collect_status(h);
+}
+
+smap_status smap_pf_run_batch(smap_handle* h, const float* y_all, const int* T_per_seq, const int* N_per_seq,
+                              float* path, double* J, int on_device) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    if (!y_all) return fail(h, SMAP_E_INVAL, "y_all is null");
+    st = upload_counts(h, T_per_seq, N_per_seq);
+    if (st) return st;
+    if (!h->pf_x64) {
+        if (cudaMalloc(&h->pf_x64, sizeof(double) * (size_t)h->B * h->Nmax * h->d) != cudaSuccess ||
+            cudaMalloc(&h->pf_lw, sizeof(double) * (size_t)h->B * h->Nmax) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, SMAP_E_NOMEM, "PF-MAP-Seq: cudaMalloc failed");
+        }
+    }
+    SMAP_CUDA(h, cudaMemcpyAsync(h->y, y_all, sizeof(float) * (size_t)h->B * h->maxT * h->dy,
+                                 kind_in(on_device), h->stream));
+    st = reset_device_state(h);
+    if (st) return st;
+    const int v = h->Nmax <= 1024 ? 0 : 1;
+    const void* fn = h->K->pf[v];
+    const int nt = round_up(v == 0 ? h->Nmax : (h->Nmax + 3) / 4, 32);
+    const size_t smem = smem_layout(h->Nmax, h->K->DP).total;
+    st = configure_kernel(h, fn, smem);
+    if (st) return st;
+    int occ = 0;
+    SMAP_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nt, smem));
+    if (occ < 1) return fail(h, SMAP_E_UNSUPPORTED, "PF-MAP-Seq kernel does not fit on an SM");
+    PfArgs a;
+    memset(&a, 0, sizeof(a));
+    a.mp = h->mp;
+    a.B = h->B;
+    a.Nmax = h->Nmax;
+    a.maxT = h->maxT;
+    a.seed = h->cfg.seed;
+    a.y = h->y;
+    a.x0 = h->x0;
+    a.hist = h->hist;
+    a.psi = h->psi;
+    a.phi = h->phi;
+    a.tcur = h->tcur;
+    a.Nseq = h->Nseq;
+    a.Tend = h->Tend;
+    a.order = h->order;
+    a.f64 = h->f64;
+    a.x64 = h->pf_x64;
+    a.lw = h->pf_lw;
+    a.status = h->status;
+    a.queue = h->queue;
+    const int grid = std::max(1, std::min(h->B, occ * h->num_sms));
+    void* args[] = {&a};
+    SMAP_CUDA(h, cudaMemsetAsync(a.queue, 0, sizeof(int), h->stream));
+    SMAP_CUDA(h, cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, smem, h->stream));
+    SMAP_CUDA(h, cudaGetLastError());
+    g_launches.fetch_add(1);
+    h->last_threads = nt;
+    h->last_grid = grid;
+    st = launch_backtrack(h);
+    if (st) return st;
+    for (int b = 0; b < h->B; ++b) h->tcur_h[b] = h->Tend_h[b];
     st = copy_outputs(h, path, J, on_device);
     if (st) return st;
     return collect_status(h);

@@ -1,6 +1,7 @@
 // Step-kernel instantiations for ModelClutterCV.
 #include "smap_internal.h"
 #include "smap_kernels.cuh"
+#include "smap_pf.cuh"
 
 namespace smap {
 
@@ -18,6 +19,8 @@ ModelKernels kernels_clutter_cv() {
     k.dbg[1] = (const void*)debug_svgd_kernel<M, 2, 512, 1>;
     k.dbg[2] = (const void*)debug_svgd_kernel<M, 4, 256, 1>;
     k.dbg[3] = (const void*)debug_svgd_kernel<M, 2, 256, 4>;
+    k.pf[0] = (const void*)pf_seq_kernel<M, 1, 1024>;
+    k.pf[1] = (const void*)pf_seq_kernel<M, 4, 1024>;
     return k;
 }
 

@@ -21,6 +21,7 @@ struct ModelKernels {
     int kind, D, DP;
     const void* seq[kNumVariants];   // seq_kernel<M, ...>
     const void* dbg[kNumVariants];   // debug_svgd_kernel<M, ...>
+    const void* pf[2];               // pf_seq_kernel<M, 1, 1024> (N <= 1024), <M, 4, 1024> (N <= 4096)
 };
 
 ModelKernels kernels_ngm1d();
