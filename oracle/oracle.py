@@ -27,7 +27,7 @@ _lib = None
 
 MODEL_NGM1D, MODEL_RANGE_CV2D, MODEL_CLUTTER_CV2D, MODEL_PLANAR_ARM, MODEL_LINEAR_GAUSS = 1, 2, 3, 4, 5
 BW_MEDIAN_ITER, BW_MEDIAN_STEP, BW_FIXED = 0, 1, 2
-PRIOR_MIXTURE, PRIOR_MEANGRAD = 0, 1
+PRIOR_MIXTURE, PRIOR_MEANGRAD, PRIOR_MAPCOND = 0, 1, 2
 
 _D = ctypes.POINTER(ctypes.c_double)
 _I = ctypes.POINTER(ctypes.c_int)
@@ -83,12 +83,12 @@ def lib():
             L.om_median_sqdist.restype = ctypes.c_double
             L.om_bandwidth.argtypes = [_D, ctypes.c_int, ctypes.c_int, ctypes.c_double]
             L.om_bandwidth.restype = ctypes.c_double
-            L.om_grad_prior.argtypes = [P, ctypes.c_int, _D, ctypes.c_int, _D, _D]
-            L.om_svgd_iteration.argtypes = [P, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_int,
+            L.om_grad_prior.argtypes = [P, ctypes.c_int, _D, _D, ctypes.c_int, _D, _D]
+            L.om_svgd_iteration.argtypes = [P, ctypes.c_int, ctypes.c_int, _D, _D, _D, ctypes.c_int,
                                             _D, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_int]
             L.om_svgd_iters.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
-                                        _D, _D, ctypes.c_int, _D, ctypes.c_int, ctypes.c_int,
+                                        _D, _D, _D, ctypes.c_int, _D, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, _D, ctypes.c_int]
             L.om_forward.argtypes = [P, ctypes.c_int, _D, _D, ctypes.c_int, _D, _D, ctypes.c_int,
                                      _I, _D]
@@ -171,23 +171,32 @@ class Model:
         x = _f64(x); f = _f64(f)
         return lib().om_logtrans(self.ref, _dp(x), _dp(f))
 
-    def grad_prior(self, prior, fprev, x):
+    @staticmethod
+    def _phi(phiprev, Np):
+        """The previous step's scores phi_{t-1} (MAP-conditioned prior); None = zeros."""
+        return _f64(np.zeros(Np) if phiprev is None else phiprev).reshape(Np)
+
+    def grad_prior(self, prior, fprev, x, phiprev=None):
         fprev = _f64(fprev).reshape(-1, self.d); x = _f64(x); g = np.empty(self.d)
-        lib().om_grad_prior(self.ref, int(prior), _dp(fprev), fprev.shape[0], _dp(x), _dp(g))
+        ph = self._phi(phiprev, fprev.shape[0])
+        lib().om_grad_prior(self.ref, int(prior), _dp(fprev), _dp(ph), fprev.shape[0], _dp(x), _dp(g))
         return g
 
-    def svgd_iteration(self, prior, t, z, fprev, x, h, eps, kernel=KERNEL_RBF):
+    def svgd_iteration(self, prior, t, z, fprev, x, h, eps, kernel=KERNEL_RBF, phiprev=None):
         fprev = _f64(fprev).reshape(-1, self.d); x = _f64(x).reshape(-1, self.d).copy(); z = _f64(z)
-        lib().om_svgd_iteration(self.ref, int(prior), int(t), _dp(z), _dp(fprev), fprev.shape[0],
+        ph = self._phi(phiprev, fprev.shape[0])
+        lib().om_svgd_iteration(self.ref, int(prior), int(t), _dp(z), _dp(fprev), _dp(ph), fprev.shape[0],
                                 _dp(x), x.shape[0], float(h), float(eps), int(kernel))
         return x
 
-    def svgd_iters(self, prior, bw_rule, bw_value, t, z, fprev, x, L, eps, kernel=KERNEL_RBF):
-        """L SVGD iterations from x (given f_t of the previous set). Returns (x, h[L])."""
+    def svgd_iters(self, prior, bw_rule, bw_value, t, z, fprev, x, L, eps, kernel=KERNEL_RBF, phiprev=None):
+        """L SVGD iterations from x (given f_t of the previous set and, for the
+        MAP-conditioned prior, its scores phi_{t-1}). Returns (x, h[L])."""
         fprev = _f64(fprev).reshape(-1, self.d); x = _f64(x).reshape(-1, self.d).copy(); z = _f64(z)
+        ph = self._phi(phiprev, fprev.shape[0])
         h = np.empty(max(int(L), 1))
         lib().om_svgd_iters(self.ref, int(prior), int(bw_rule), float(bw_value), int(t), _dp(z),
-                            _dp(fprev), fprev.shape[0], _dp(x), x.shape[0], int(L), float(eps), _dp(h),
+                            _dp(fprev), _dp(ph), fprev.shape[0], _dp(x), x.shape[0], int(L), float(eps), _dp(h),
                             int(kernel))
         return x, h[: int(L)]
 

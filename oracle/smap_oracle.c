@@ -24,10 +24,13 @@
  *     formula; h = s * med / log(N) with med the median of the squared pairwise
  *     distances over i<k (mean of the two middle values when their number is
  *     even), s a scale (1 = plain heuristic). N = 1 or med = 0: h = 1.
- *   - Prior term of Eq. (SVGD_newupdate): two readings. MIXTURE (default): the
+ *   - Prior term of Eq. (SVGD_newupdate): three readings. MIXTURE (default): the
  *     score of log (1/N) sum_j p(x | x_{t-1}^j), i.e. responsibilities w_kj;
  *     MEANGRAD (literal average of the N gradients): Q^-1 (mean_j f_j - x).
- *     The two coincide when the previous set has one particle (t = 1).
+ *     MAPCOND (the prior conditioned on the previous MAP estimates that
+ *     Section V-C describes): the score of max_j [phi_{t-1}(j) +
+ *     log p(x | x_{t-1}^j)], i.e. Q^-1 (f_{j*} - x) for the maximising j*.
+ *     The three coincide when the previous set has one particle (t = 1).
  *   - Initial particles at step t (unspecified): x_t^{i,(0)} = f_t(x_{t-1}^i)
  *     + sqrt(q) (.) xi_i, xi ~ N(0, I) from Philox-4x32-10 (Salmon et al.
  *     2011) keyed by the seed, counter (i, t, seq, block), Box-Muller in FP64.
@@ -50,7 +53,7 @@
 enum { OM_NGM1D = 1, OM_RANGE_CV2D = 2, OM_CLUTTER_CV2D = 3, OM_PLANAR_ARM = 4,
        OM_LINEAR_GAUSS = 5, OM_RANGE_ZV2D = 6, OM_SE2_RB = 7 };
 enum { OM_BW_MEDIAN_ITER = 0, OM_BW_MEDIAN_STEP = 1, OM_BW_FIXED = 2 };
-enum { OM_PRIOR_MIXTURE = 0, OM_PRIOR_MEANGRAD = 1 };
+enum { OM_PRIOR_MIXTURE = 0, OM_PRIOR_MEANGRAD = 1, OM_PRIOR_MAPCOND = 2 };
 
 static const double OM_PI = 3.14159265358979323846;
 
@@ -514,11 +517,25 @@ static void om_kernel(int kernel, const double* a, const double* b, int d, doubl
 /* ------------------------------------------------------------------------ */
 
 /* grad_x of the prior term. fprev[j] = f_t(x_{t-1}^j), j < Np. */
-void om_grad_prior(const om_model* m, int prior, const double* fprev, int Np,
+void om_grad_prior(const om_model* m, int prior, const double* fprev, const double* phiprev, int Np,
                    const double* x, double* g)
 {
     int d = m->d;
     for (int c = 0; c < d; ++c) g[c] = 0.0;
+    if (prior == OM_PRIOR_MAPCOND) {
+        /* MAP-conditioned (the prior conditioned on the previous MAP estimates,
+         * Section V-C): the score of max_j [phi_{t-1}(j) + log N(x; f_j, Q)],
+         * i.e. Q^-1 (f_{j*} - x) with j* that maximiser (lowest j on ties);
+         * phiprev NULL counts as all zeros. */
+        int best = 0;
+        double bv = -INFINITY;
+        for (int j = 0; j < Np; ++j) {
+            double v = (phiprev ? phiprev[j] : 0.0) + om_logtrans(m, x, fprev + (long)j * d);
+            if (v > bv) { bv = v; best = j; }
+        }
+        for (int c = 0; c < d; ++c) g[c] = (fprev[(long)best * d + c] - x[c]) / m->q[c];
+        return;
+    }
     if (prior == OM_PRIOR_MEANGRAD) {
         /* (1/Np) sum_j grad log N(x; f_j, Q) = Q^-1 (mean_j f_j - x) */
         for (int j = 0; j < Np; ++j)
@@ -545,24 +562,24 @@ void om_grad_prior(const om_model* m, int prior, const double* fprev, int Np,
 
 /* grad_x log p(z_t, x | previous set) at one particle. */
 static void om_score(const om_model* m, int prior, int t, const double* z,
-                     const double* fprev, int Np, const double* x, double* g)
+                     const double* fprev, const double* phiprev, int Np, const double* x, double* g)
 {
     double gl[OM_MAXD], gp[OM_MAXD];
     om_grad_loglik(m, t, z, x, gl);
-    om_grad_prior(m, prior, fprev, Np, x, gp);
+    om_grad_prior(m, prior, fprev, phiprev, Np, x, gp);
     for (int c = 0; c < m->d; ++c) g[c] = gl[c] + gp[c];
 }
 
 /* One SVGD iteration (Algorithm 1, Eq. svgd_iterate with the score of
  * Eq. SVGD_initial_newupdate / SVGD_newupdate): all particles move together. */
 void om_svgd_iteration(const om_model* m, int prior, int t, const double* z,
-                       const double* fprev, int Np, double* x, int N,
+                       const double* fprev, const double* phiprev, int Np, double* x, int N,
                        double h, double eps, int kernel)
 {
     int d = m->d;
     double* g = (double*)malloc(sizeof(double) * N * d);
     double* phi = (double*)calloc((size_t)N * d, sizeof(double));
-    for (int k = 0; k < N; ++k) om_score(m, prior, t, z, fprev, Np, x + (long)k * d, g + (long)k * d);
+    for (int k = 0; k < N; ++k) om_score(m, prior, t, z, fprev, phiprev, Np, x + (long)k * d, g + (long)k * d);
     for (int i = 0; i < N; ++i) {
         const double* xi = x + (long)i * d;
         for (int k = 0; k < N; ++k) {
@@ -585,7 +602,7 @@ void om_svgd_iteration(const om_model* m, int prior, int t, const double* z,
 /* L SVGD iterations at step t from the given initial particles.
  * h_out[l] receives the bandwidth used at iteration l (may be NULL). */
 void om_svgd_iters(const om_model* m, int prior, int bw_rule, double bw_value,
-                   int t, const double* z, const double* fprev, int Np,
+                   int t, const double* z, const double* fprev, const double* phiprev, int Np,
                    double* x, int N, int L, double eps, double* h_out, int kernel)
 {
     double h = 1.0;
@@ -593,7 +610,7 @@ void om_svgd_iters(const om_model* m, int prior, int bw_rule, double bw_value,
         if (bw_rule == OM_BW_FIXED) h = bw_value;
         else if (bw_rule == OM_BW_MEDIAN_ITER || l == 0) h = om_bandwidth(x, N, m->d, bw_value);
         if (h_out) h_out[l] = h;
-        om_svgd_iteration(m, prior, t, z, fprev, Np, x, N, h, eps, kernel);
+        om_svgd_iteration(m, prior, t, z, fprev, phiprev, Np, x, N, h, eps, kernel);
     }
 }
 
@@ -696,7 +713,7 @@ int om_run_sequence(const om_run_cfg* cfg, uint32_t seq, const double* x0, int T
             const double* fi = fprev + (long)(Np == 1 ? 0 : i) * d;
             for (int c = 0; c < d; ++c) x[(long)i * d + c] = fi[c] + sqrt(m.q[c]) * xi[c];
         }
-        om_svgd_iters(&m, cfg->prior, cfg->bw_rule, cfg->bw_value, t, zt, fprev, Np,
+        om_svgd_iters(&m, cfg->prior, cfg->bw_rule, cfg->bw_value, t, zt, fprev, phi_prev, Np,
                       x, N, cfg->L, cfg->eps, NULL, cfg->kernel);
         om_forward(&m, t, zt, fprev, Np, phi_prev, x, N, psi_t, phi);
         memcpy(H + (size_t)(t - 1) * N * d, x, sizeof(double) * N * d);

@@ -216,3 +216,36 @@ def test_grad_prior_mixture_and_meangrad(oracle):
             assert ga[c] == pytest.approx((mean(x + e) - mean(x - e)) / 2e-6, rel=1e-5, abs=1e-4)
         if Np == 1:
             assert np.allclose(gm, ga, rtol=1e-14, atol=0)
+
+
+def test_grad_prior_map_conditioned(oracle):
+    """MAPCOND = gradient of max_j [phi_j + log N(x; f_j, Q)] (central finite
+    differences of scipy densities where the best j is clear); one previous
+    particle gives the mixture's gradient; a dominant phi_j selects that
+    component alone."""
+    rng = np.random.default_rng(6)
+    m = oracle.Model(5, W.linear_params())
+    q = m.q
+    for Np in (1, 4, 23):
+        fprev = rng.normal(0, 0.3, (Np, 4))
+        phi = rng.normal(0, 2.0, Np)
+        for _ in range(5):
+            x = rng.normal(0, 0.3, 4)
+
+            def env(v):
+                return np.max(phi + np.atleast_1d(stats.multivariate_normal.logpdf(fprev, v, np.diag(q))))
+
+            vals = np.sort(phi + np.atleast_1d(stats.multivariate_normal.logpdf(fprev, x, np.diag(q))))
+            if Np > 1 and vals[-1] - vals[-2] < 1e-2:
+                continue
+            g = m.grad_prior(2, fprev, x, phi)
+            for c in range(4):
+                e = np.zeros(4); e[c] = 1e-7
+                assert g[c] == pytest.approx((env(x + e) - env(x - e)) / 2e-7, rel=1e-5, abs=1e-4)
+        if Np == 1:
+            x = rng.normal(0, 0.3, 4)
+            assert np.allclose(m.grad_prior(2, fprev, x, phi), m.grad_prior(0, fprev, x), rtol=1e-14, atol=0)
+    fprev = rng.normal(0, 0.3, (5, 4))
+    phi = np.zeros(5); phi[3] = 1e4
+    x = rng.normal(0, 0.3, 4)
+    assert np.allclose(m.grad_prior(2, fprev, x, phi), (fprev[3] - x) / q, rtol=1e-14, atol=0)
