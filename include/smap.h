@@ -101,8 +101,12 @@ typedef enum { SMAP_BW_MEDIAN_ITER = 0, SMAP_BW_MEDIAN_STEP = 1, SMAP_BW_FIXED =
 /* Prior term of the direction of Eq. SVGD_newupdate:
  *   MIXTURE   score of log (1/N) sum_j p(x | x_{t-1}^j) (responsibility-weighted)
  *   MEANGRAD  mean over j of grad log p(x | x_{t-1}^j) = Q^-1 (mean_j f_j - x)
+ *   MAPCOND   conditioned on the previous MAP estimates (Section V-C): the
+ *             score of max_j [phi_{t-1}(j) + log p(x | x_{t-1}^j)], i.e.
+ *             Q^-1 (f_{j*} - x) for the maximising predecessor j* (chosen in
+ *             FP32, lowest j on ties)
  * They coincide when the previous set has one particle (t = 1). */
-typedef enum { SMAP_PRIOR_MIXTURE = 0, SMAP_PRIOR_MEANGRAD = 1 } smap_prior;
+typedef enum { SMAP_PRIOR_MIXTURE = 0, SMAP_PRIOR_MEANGRAD = 1, SMAP_PRIOR_MAPCOND = 2 } smap_prior;
 
 /* Stein kernel k(x, x') of the SVGD direction (Eq. svgd_iterate), u = r^2 / h
  * with r = |x - x'| and h the bandwidth of smap_bw_rule:
@@ -316,12 +320,13 @@ smap_status smap_get_variant(const smap_handle* h, int* variant, int* threads, i
  * the given initial particles x_init [B][N][d] with the prior built from the
  * previous set x_prev [B][n_prev][d] (n_prev = 1 and t = 1: x_prev holds
  * x_0^true, whose transition is taken in FP64 from the handle's x0 instead),
- * observation y [B][dy]. Writes x_out [B][N][d] and the bandwidth of each
- * iteration h_out [B][n_iters] (may be NULL). Does not change the handle's
- * state. */
+ * observation y [B][dy], and for the MAP-conditioned prior the previous
+ * scores phi_prev [B][n_prev] FP64 (NULL = zeros). Writes x_out [B][N][d] and
+ * the bandwidth of each iteration h_out [B][n_iters] (may be NULL). Does not
+ * change the handle's state. */
 smap_status smap_debug_svgd(smap_handle* h, int t, const float* x_prev, int n_prev,
                             const float* x_init, const float* y, int n_iters,
-                            float* x_out, float* h_out);
+                            float* x_out, float* h_out, const double* phi_prev);
 
 /* Raw Philox-4x32-10 words for counters (c0 + k, c1, c2, c3), k < n, key
  * (key0, key1): out [n][4]; and the standard normals the step kernels draw

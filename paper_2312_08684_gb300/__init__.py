@@ -105,8 +105,8 @@ class Estimator:
         abi.smap_viterbi(self.h, hist, y_all, T, Nseq, path, J, psi)
         return path, J, psi
 
-    def debug_svgd(self, t, x_prev, x_init, y, n_iters):
-        return abi.smap_debug_svgd(self.h, t, x_prev, x_init, y, n_iters)
+    def debug_svgd(self, t, x_prev, x_init, y, n_iters, phi_prev=None):
+        return abi.smap_debug_svgd(self.h, t, x_prev, x_init, y, n_iters, phi_prev)
 
     def autotune(self, y_all, sample, steps):
         return abi.smap_autotune(self.h, y_all, sample, steps)

@@ -20,7 +20,7 @@ SMAP_OK, SMAP_E_INVAL, SMAP_E_NOMEM, SMAP_E_CUDA, SMAP_E_STATE, SMAP_E_TIMEOUT, 
 SMAP_MODEL_NGM1D, SMAP_MODEL_RANGE_CV2D, SMAP_MODEL_CLUTTER_CV2D, SMAP_MODEL_PLANAR_ARM, \
     SMAP_MODEL_LINEAR_GAUSS = 1, 2, 3, 4, 5
 SMAP_BW_MEDIAN_ITER, SMAP_BW_MEDIAN_STEP, SMAP_BW_FIXED = 0, 1, 2
-SMAP_PRIOR_MIXTURE, SMAP_PRIOR_MEANGRAD = 0, 1
+SMAP_PRIOR_MIXTURE, SMAP_PRIOR_MEANGRAD, SMAP_PRIOR_MAPCOND = 0, 1, 2
 
 # Every symbol include/smap.h declares (the CPU tests check the library exports them).
 EXPORTS = [
@@ -91,7 +91,7 @@ def load():
     L.smap_num_variants.argtypes = []
     L.smap_variant_info.argtypes = [_I, ctypes.POINTER(_I), ctypes.POINTER(_I)]
     L.smap_get_variant.argtypes = [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]
-    L.smap_debug_svgd.argtypes = [_VP, _I, _VP, _I, _VP, _VP, _I, _VP, _VP]
+    L.smap_debug_svgd.argtypes = [_VP, _I, _VP, _I, _VP, _VP, _I, _VP, _VP, _VP]
     u32 = ctypes.c_uint32
     L.smap_debug_philox.argtypes = [u32, u32, u32, u32, u32, u32, _I, _VP]
     L.smap_debug_normals.argtypes = [ctypes.c_uint64, u32, u32, u32, _I, _I, _VP]
@@ -318,16 +318,18 @@ def smap_get_variant(h):
     return v.value, t.value, g.value
 
 
-def smap_debug_svgd(h, t, x_prev, x_init, y, n_iters):
+def smap_debug_svgd(h, t, x_prev, x_init, y, n_iters, phi_prev=None):
     x_prev = np.ascontiguousarray(x_prev, np.float32)
     x_init = np.ascontiguousarray(x_init, np.float32)
     y = np.ascontiguousarray(y, np.float32)
+    ph = None if phi_prev is None else np.ascontiguousarray(phi_prev, np.float64)
     x_out = np.empty_like(x_init)
     h_out = np.empty((x_init.shape[0], max(int(n_iters), 1)), np.float32)
     _check(load().smap_debug_svgd(h, int(t), ctypes.c_void_p(x_prev.ctypes.data), int(x_prev.shape[1]),
                                   ctypes.c_void_p(x_init.ctypes.data), ctypes.c_void_p(y.ctypes.data),
                                   int(n_iters), ctypes.c_void_p(x_out.ctypes.data),
-                                  ctypes.c_void_p(h_out.ctypes.data)), h)
+                                  ctypes.c_void_p(h_out.ctypes.data),
+                                  None if ph is None else ctypes.c_void_p(ph.ctypes.data)), h)
     return x_out, h_out[:, : int(n_iters)]
 
 

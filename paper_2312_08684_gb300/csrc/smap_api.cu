@@ -686,7 +686,7 @@ smap_status smap_create(const smap_config* cfg, smap_handle** out) {
     if (!(std::isfinite(cfg->step))) return bail(SMAP_E_INVAL, "step not finite");
     if (cfg->bw_rule < 0 || cfg->bw_rule > 2) return bail(SMAP_E_INVAL, "bw_rule");
     if (!(cfg->bw_value > 0) || !std::isfinite(cfg->bw_value)) return bail(SMAP_E_INVAL, "bw_value must be > 0");
-    if (cfg->prior < 0 || cfg->prior > 1) return bail(SMAP_E_INVAL, "prior");
+    if (cfg->prior < 0 || cfg->prior > 2) return bail(SMAP_E_INVAL, "prior");
     if (cfg->kernel < 0 || cfg->kernel > 2) return bail(SMAP_E_INVAL, "kernel");
     if (!cfg->x0) return bail(SMAP_E_INVAL, "x0 is null");
     h->B = cfg->batch;
@@ -1076,25 +1076,27 @@ smap_status smap_autotune(smap_handle* h, const float* y_all, int sample, int st
 }
 
 smap_status smap_debug_svgd(smap_handle* h, int t, const float* x_prev, int n_prev, const float* x_init,
-                            const float* y, int n_iters, float* x_out, float* h_out) {
+                            const float* y, int n_iters, float* x_out, float* h_out, const double* phi_prev) {
     smap_status st = check_usable(h);
     if (st) return st;
     if (!x_prev || !x_init || !y || !x_out || t < 1 || n_iters < 0) return fail(h, SMAP_E_INVAL, "debug_svgd: bad arguments");
     if (n_prev != 1 && n_prev != h->Nmax) return fail(h, SMAP_E_INVAL, "debug_svgd: n_prev must be 1 or N");
     const size_t B = h->B, N = h->Nmax, d = h->d;
     float *dxp = nullptr, *dxi = nullptr, *dy = nullptr, *dxo = nullptr, *dho = nullptr;
-    double* df = nullptr;
-    auto cleanup = [&]() { cudaFree(dxp); cudaFree(dxi); cudaFree(dy); cudaFree(dxo); cudaFree(dho); cudaFree(df); };
+    double *df = nullptr, *dph = nullptr;
+    auto cleanup = [&]() { cudaFree(dxp); cudaFree(dxi); cudaFree(dy); cudaFree(dxo); cudaFree(dho); cudaFree(df); cudaFree(dph); };
     cudaError_t e = cudaSuccess;
     if ((e = cudaMalloc(&dxp, sizeof(float) * B * n_prev * d)) || (e = cudaMalloc(&dxi, sizeof(float) * B * N * d)) ||
         (e = cudaMalloc(&dy, sizeof(float) * B * h->dy)) || (e = cudaMalloc(&dxo, sizeof(float) * B * N * d)) ||
-        (e = cudaMalloc(&dho, sizeof(float) * B * std::max(n_iters, 1))) || (e = cudaMalloc(&df, sizeof(double) * B * n_prev * d))) {
+        (e = cudaMalloc(&dho, sizeof(float) * B * std::max(n_iters, 1))) || (e = cudaMalloc(&df, sizeof(double) * B * n_prev * d)) ||
+        (phi_prev && (e = cudaMalloc(&dph, sizeof(double) * B * n_prev)))) {
         cleanup();
         return cuda_fail(h, e, "debug_svgd cudaMalloc");
     }
     cudaMemcpy(dxp, x_prev, sizeof(float) * B * n_prev * d, cudaMemcpyHostToDevice);
     cudaMemcpy(dxi, x_init, sizeof(float) * B * N * d, cudaMemcpyHostToDevice);
     cudaMemcpy(dy, y, sizeof(float) * B * h->dy, cudaMemcpyHostToDevice);
+    if (phi_prev) cudaMemcpy(dph, phi_prev, sizeof(double) * B * n_prev, cudaMemcpyHostToDevice);
     DebugSvgdArgs a;
     memset(&a, 0, sizeof(a));
     a.mp = h->mp;
@@ -1102,6 +1104,7 @@ smap_status smap_debug_svgd(smap_handle* h, int t, const float* x_prev, int n_pr
     a.bw_rule = h->cfg.bw_rule; a.prior = h->cfg.prior; a.kernel = h->cfg.kernel;
     a.eps = (float)h->cfg.step; a.bw_value = (float)h->cfg.bw_value;
     a.xprev = dxp; a.x0 = h->x0; a.xinit = dxi; a.y = dy; a.xout = dxo; a.hout = dho; a.f64 = df;
+    a.phiprev = dph;
     const int v = h->variant >= 0 ? h->variant : heuristic_variant(h);
     const int nt = variant_threads(v, h->Nmax);
     const size_t smem = smem_layout(h->Nmax, h->K->DP).total;

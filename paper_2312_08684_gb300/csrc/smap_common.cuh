@@ -71,6 +71,7 @@ struct DebugSvgdArgs {
     float* xout;              // [B][N][d]
     float* hout;              // [B][iters]
     double* f64;              // [B][Np][d] scratch
+    const double* phiprev;    // [B][Np] previous scores (MAP-conditioned prior), or null = zeros
     int kernel;               // Stein kernel: 0 RBF, 1 IMQ, 2 Matern 3/2
 };
 

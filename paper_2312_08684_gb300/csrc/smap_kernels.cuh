@@ -32,7 +32,7 @@ constexpr float kLam = 1.3862943611198906f;    // 1 / kKm^2 = 2 ln 2
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct SmemLayout {
-    size_t phis, xs, gs, fs, nrm, cand, zs, red, misc, total;
+    size_t phis, xs, gs, fs, nrm, phf, cand, zs, red, misc, total;
 };
 
 // Dynamic shared memory of the step kernels for Nmax particles of stride DP.
@@ -44,6 +44,7 @@ __host__ __device__ inline SmemLayout smem_layout(int Nmax, int DP) {
     L.gs = off;   off = align16(off + sizeof(float) * Nmax * (DP < 2 ? 2 : DP));
     L.fs = off;   off = align16(off + sizeof(float) * Nmax * DP);
     L.nrm = off;  off = align16(off + sizeof(float) * Nmax);
+    L.phf = off;  off = align16(off + sizeof(float) * Nmax);
     L.cand = off; off = align16(off + sizeof(uint32_t) * kCandCap);
     L.zs = off;   off = align16(off + sizeof(float) * kMaxDy);
     L.red = off;  off = align16(off + sizeof(double) * 40);
@@ -58,6 +59,7 @@ struct Sm {
     float* gs;      // w_k = A g_k - Bc x^_k [N][DP]; later (A+, A-) of the recursion screen
     float* fs;      // (f_t(x_{t-1}^j) - c) Q^-1/2 kKm, [Np][DP]
     float* nrm;     // |x^_k|^2 of the scaled particles
+    float* phf;     // (phi_{t-1}(j) - max) log2(e) in FP32 (MAP-conditioned prior)
     uint32_t* cand; // median candidates / histograms
     float* zs;      // observation z_t
     double* redd;   // reduction scratch (aliases redi / redf)
@@ -75,6 +77,7 @@ __device__ inline Sm bind_smem(unsigned char* base, int Nmax, int DP) {
     s.gs = reinterpret_cast<float*>(base + L.gs);
     s.fs = reinterpret_cast<float*>(base + L.fs);
     s.nrm = reinterpret_cast<float*>(base + L.nrm);
+    s.phf = reinterpret_cast<float*>(base + L.phf);
     s.cand = reinterpret_cast<uint32_t*>(base + L.cand);
     s.zs = reinterpret_cast<float*>(base + L.zs);
     s.redd = reinterpret_cast<double*>(base + L.red);
@@ -593,6 +596,35 @@ __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const S
         load_row<D, DP>(s.fs, Np == 1 ? 0 : min(ii, Np - 1), fr);
         Mref[p] = sqdist<D>(xt[p], fr);
     }
+    if (prior == 2) {
+        // MAP-conditioned: the predecessor j maximising phi_{t-1}(j) + log
+        // p(x_i | x_{t-1}^j), i.e. phf_j - |x~_i - f~_j|^2 in log2 units (FP32,
+        // lowest j on ties); its transition alone gives the prior score
+        float bv[PPT];
+        int bj[PPT];
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) { bv[p] = -INFINITY; bj[p] = 0; }
+        for (int j = 0; j < Np; ++j) {
+            float fj[D];
+            load_row<D, DP>(s.fs, j, fj);
+            const float pj = s.phf[j];
+#pragma unroll
+            for (int p = 0; p < PPT; ++p) {
+                const float v = pj - sqdist<D>(xt[p], fj);
+                const bool nb = v > bv[p];
+                bv[p] = nb ? v : bv[p];
+                bj[p] = nb ? j : bj[p];
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            float fj[D];
+            load_row<D, DP>(s.fs, bj[p], fj);
+            S[p] = 1.0f;
+#pragma unroll
+            for (int c = 0; c < D; ++c) A[p][c] = xt[p][c] - fj[c];
+        }
+    }
     if (prior == 0) {
         // mixture responsibilities w_ij = 2^(Mref - |x~_i - f~_j|^2) / sum:
         // the parent's term is 1, so the sum is >= 1; a sum above 2^100 (a
@@ -653,7 +685,7 @@ __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const S
         for (int c = 0; c < D; ++c) x[c] = fmaf(xh[c], inv_sc, cf[c]);
         M::grad_loglik(mp, s.zs, x, g);
         // Q^-1 (f - x) = -(Q^-1/2 / kKm) (x~ - f~)
-        if (prior == 0) {
+        if (prior != 1) {
             const float inv = 1.0f / S[p];
 #pragma unroll
             for (int c = 0; c < D; ++c) g[c] -= mp.sqrt_qinv_f[c] * (1.0f / kKm) * A[p][c] * inv;
@@ -813,6 +845,13 @@ __device__ void svgd_iterations(const ModelParams& mp, const Sm& s, int N, int N
     float cf[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) cf[c] = s.misc[c];
+    if (prior == 2) {
+        // the previous scores relative to their maximum, in log2 units
+        double pmax = -INFINITY;
+        for (int j = tid; j < Np; j += NT) pmax = fmax(pmax, s.phis[j]);
+        pmax = block_max_d(pmax, s.redd);
+        for (int j = tid; j < Np; j += NT) s.phf[j] = (float)((s.phis[j] - pmax) * 1.4426950408889634);
+    }
     // centre (scale 1)
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
@@ -1139,6 +1178,7 @@ __global__ void __launch_bounds__(MAXT, MINB) debug_svgd_kernel(const __grid_con
     // the previous set goes through xs (prepare_step reads it there)
     const float* xp = a.xprev + (size_t)b * a.Np * D;
     for (int e = tid; e < a.Np * D; e += NT) s.xs[(e / D) * DP + (e % D)] = xp[e];
+    for (int j = tid; j < a.Np; j += NT) s.phis[j] = a.phiprev ? a.phiprev[(size_t)b * a.Np + j] : 0.0;
     __syncthreads();
     prepare_step<M, PPT>(a.mp, s, a.t, a.N, a.Np, first, a.x0 + (size_t)b * D, a.y + (size_t)b * a.mp.dy,
                          a.f64 + (size_t)b * a.Np * D, a.prior, 0, 0,

@@ -42,7 +42,7 @@ MODEL_NGM1D, MODEL_RANGE_CV2D, MODEL_CLUTTER_CV2D, MODEL_PLANAR_ARM, MODEL_LINEA
 MODEL_RANGE_ZV2D = 6
 MODEL_SE2_RB = 7
 BW_MEDIAN_ITER, BW_MEDIAN_STEP, BW_FIXED = 0, 1, 2
-PRIOR_MIXTURE, PRIOR_MEANGRAD = 0, 1
+PRIOR_MIXTURE, PRIOR_MEANGRAD, PRIOR_MAPCOND = 0, 1, 2
 
 
 @dataclasses.dataclass

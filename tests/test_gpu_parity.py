@@ -63,7 +63,7 @@ CASES = {
 SPREAD = {"ngm1d": 2.0, "range": 0.3, "clutter": 0.3, "arm": 0.02, "linear": 0.2, "range_zv": 0.2, "se2": 0.1}
 
 
-def _svgd_case(oracle, name, t, n_iters, prior=0, bw_rule=0, bw_value=1.0, N=None, kernel=0):
+def _svgd_case(oracle, name, t, n_iters, prior=0, bw_rule=0, bw_value=1.0, N=None, kernel=0, phi_spread=None):
     wl = CASES[name]()
     if N is not None:
         wl.N = N
@@ -83,11 +83,21 @@ def _svgd_case(oracle, name, t, n_iters, prior=0, bw_rule=0, bw_value=1.0, N=Non
         a = f[np.zeros(N, int)] if t == 1 else f
         xinit[b] = (a + np.sqrt(m.q) * rng.normal(0, 1, (N, d))).astype(np.float32)
     y = np.ascontiguousarray(wl.y[:, t - 1])
+    Np = xprev.shape[1]
+    phi = None if phi_spread is None else phi_spread * rng.normal(0, 1, (B, Np))
     with Estimator.from_workload(wl) as est:
-        xg, hg = est.debug_svgd(t, xprev, xinit, y, n_iters)
+        xg, hg = est.debug_svgd(t, xprev, xinit, y, n_iters, phi)
     for b in range(B):
         xo, ho = m.svgd_iters(prior, bw_rule, bw_value, t, y[b].astype(np.float64), fprev[b],
-                              xinit[b].astype(np.float64), n_iters, wl.step, kernel=kernel)
+                              xinit[b].astype(np.float64), n_iters, wl.step, kernel=kernel,
+                              phiprev=None if phi is None else phi[b])
+        if prior == 2 and phi is not None and Np > 1:
+            # the predecessor choice must be clear at the inputs (FP32 on the
+            # GPU, FP64 here): relative top-two margin above 1e-5
+            x64 = xinit[b].astype(np.float64)
+            for i in range(N):
+                v = np.sort([phi[b, j] + m.logtrans(x64[i], fprev[b][j]) for j in range(Np)])
+                assert (v[-1] - v[-2]) / max(1.0, abs(v[-1])) > 1e-5, "near-tie in the test input"
         yield b, xg[b], xo, hg[b], ho
 
 
@@ -103,6 +113,15 @@ def test_one_svgd_iteration_matches_oracle(oracle, name, t):
 def test_meangrad_prior_matches_oracle(oracle, name):
     for b, xg, xo, hg, ho in _svgd_case(oracle, name, 3, 1, prior=1):
         assert rel_err(xg, xo) <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["range", "linear", "ngm1d", "range_zv", "se2", "arm"])
+@pytest.mark.parametrize("t", [1, 3])
+def test_map_conditioned_prior_matches_oracle(oracle, name, t):
+    """MAP-conditioned prior: the best predecessor under phi_{t-1} + log
+    transition; seeded previous scores with a spread of 3 nats."""
+    for b, xg, xo, hg, ho in _svgd_case(oracle, name, t, 1, prior=2, phi_spread=3.0):
+        assert rel_err(xg, xo) <= 1e-5, (name, t, b, rel_err(xg, xo))
 
 
 @pytest.mark.parametrize("rule,val", [(1, 1.0), (2, 0.5), (0, 3.0), (0, 0.5)])
@@ -220,6 +239,22 @@ def test_full_run_small_matches_oracle(oracle, name):
         assert rel_err(path[b, : T + 1], ref["path"]) <= 1e-3
         assert J[b] == pytest.approx(ref["J"], rel=1e-3)
         assert np.all(np.isnan(path[b, T + 1:]))
+
+
+@pytest.mark.parametrize("name", ["range", "linear", "range_zv", "ngm1d"])
+def test_map_conditioned_full_run_matches_oracle(oracle, name):
+    wl = {"range": lambda: W.make_range_cv(B=3, T=20, N=48, L=10, dropout=(6, 10)),
+          "linear": lambda: W.make_linear_gauss(B=3, T=15, N=40, L=20),
+          "range_zv": lambda: W.make_range_zv(B=3, T=25, N=30, L=20, blocked=((8, 6),)),
+          "ngm1d": lambda: W.make_ngm1d(B=3, T=20, N=20, L=30)}[name]()
+    wl.prior = 2
+    path, J, hist, psi = _run_gpu(wl)
+    for b in range(wl.B):
+        T = int(wl.T[b])
+        ref = _run_oracle(oracle, wl, b)
+        assert rel_err(hist[b, :T], ref["hist"]) <= 1e-3
+        assert rel_err(path[b, : T + 1], ref["path"]) <= 1e-3
+        assert J[b] == pytest.approx(ref["J"], rel=1e-3)
 
 
 @pytest.mark.parametrize("kernel", [1, 2])
