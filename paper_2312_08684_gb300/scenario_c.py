@@ -1,11 +1,13 @@
 """Range-only localisation without a motion prior (the paper's Section V-C form).
 
-  python -m paper_2312_08684_gb300.scenario_c [--runs 64] [--T 600]
+  python -m paper_2312_08684_gb300.scenario_c [--runs 64] [--T 600] [--prior 0|2]
 
 2-D position, zero-velocity random walk with Q = (alpha dt)^2 I = 0.01 I, range
 measurements to three anchors with sigma_z = 0.5, anchor 1 blocked for six
 periods (2.5, 5.0, 4.0, 4.0, 3.0 and 3.5 s at 10 Hz), SVGD step 0.005 and 100
-iterations per step, transition-mixture prior, median bandwidth. The
+iterations per step, median bandwidth, and the transition-mixture prior
+(--prior 0) or the prior conditioned on the previous MAP estimates that the
+section describes (--prior 2: the best predecessor under phi_{t-1}). The
 trajectories are seeded synthetic random walks (the paper's recorded
 trajectories are not available), so the RMSE column is compared in
 magnitude only.
@@ -53,16 +55,17 @@ def main(argv=None):
     ap.add_argument("--runs", type=int, default=64)
     ap.add_argument("--T", type=int, default=600)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--prior", type=int, default=W.PRIOR_MIXTURE, choices=[0, 1, 2])
     args = ap.parse_args(argv)
     out = []
     for N, (paper_rmse, paper_ms) in PAPER.items():
-        wl1 = W.make_range_zv(B=1, T=args.T, N=N)
+        wl1 = W.make_range_zv(B=1, T=args.T, N=N, prior=args.prior)
         with Estimator.from_workload(wl1) as est:
             t1, _, _ = _timed(est, wl1.y, args.reps)
-        wl = W.make_range_zv(B=args.runs, T=args.T, N=N)
+        wl = W.make_range_zv(B=args.runs, T=args.T, N=N, prior=args.prior)
         with Estimator.from_workload(wl) as est:
             tb, path, J = _timed(est, wl.y, args.reps)
-        r = {"N": N, "L": wl.L, "T": args.T, "runs": args.runs,
+        r = {"N": N, "L": wl.L, "T": args.T, "runs": args.runs, "prior": args.prior,
              "ms_per_step_single": 1e3 * t1 / args.T, "paper_ms_per_step": paper_ms,
              "seq_steps_per_s_batched": args.runs * args.T / tb,
              "rmse": rmse_of(path, wl.truth), "paper_rmse": paper_rmse,
