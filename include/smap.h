@@ -302,7 +302,12 @@ smap_status smap_proposal_capture(smap_proposal* p, smap_handle* h, float* feat,
  * must outlive the attachment. */
 smap_status smap_set_proposal(smap_handle* h, smap_proposal* p, int L_learned);
 
-/* Kernel variant (particles per thread, block size) used by the step kernels.
+/* Kernel variant (particles per thread, block-size bound, threads per
+ * particle) used by the step kernels. With threads per particle > 1 the lanes
+ * of a group split one particle's sums over the other particles (shorter
+ * serial chains: the built-in choice when there are fewer sequences than SMs);
+ * those variants sum in a different order, so their results agree with the
+ * others to rounding, not bit for bit.
  * smap_autotune times every compiled variant on the first min(B, sample)
  * sequences for `steps` steps of y_all (layout as in smap_run_batch, host or
  * device per on_device) and keeps the fastest; the handle is reset afterwards.
@@ -312,7 +317,8 @@ smap_status smap_autotune(smap_handle* h, const float* y_all, int sample, int st
                           int n_ms);
 smap_status smap_set_variant(smap_handle* h, int variant);
 int smap_num_variants(void);
-smap_status smap_variant_info(int variant, int* particles_per_thread, int* max_threads);
+smap_status smap_variant_info(int variant, int* particles_per_thread, int* max_threads,
+                              int* threads_per_particle);
 smap_status smap_get_variant(const smap_handle* h, int* variant, int* threads, int* grid);
 
 /* Debug / parity entry points (host pointers, synchronous).

@@ -89,7 +89,7 @@ def load():
     L.smap_autotune.argtypes = [_VP, _VP, _I, _I, _I, ctypes.POINTER(_I), _VP, _I]
     L.smap_set_variant.argtypes = [_VP, _I]
     L.smap_num_variants.argtypes = []
-    L.smap_variant_info.argtypes = [_I, ctypes.POINTER(_I), ctypes.POINTER(_I)]
+    L.smap_variant_info.argtypes = [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]
     L.smap_get_variant.argtypes = [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]
     L.smap_debug_svgd.argtypes = [_VP, _I, _VP, _I, _VP, _VP, _I, _VP, _VP, _VP]
     u32 = ctypes.c_uint32
@@ -307,9 +307,10 @@ def smap_num_variants():
 
 
 def smap_variant_info(v):
-    a, b = ctypes.c_int(), ctypes.c_int()
-    _check(load().smap_variant_info(int(v), ctypes.byref(a), ctypes.byref(b)))
-    return a.value, b.value
+    """(particles per thread, block-size bound, threads per particle)."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().smap_variant_info(int(v), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
 
 
 def smap_get_variant(h):

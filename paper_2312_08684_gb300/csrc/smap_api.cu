@@ -206,13 +206,20 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 // Block size of variant v for Nmax particles, or 0 if the variant cannot hold them.
 int variant_threads(int v, int Nmax) {
     const VariantInfo& vi = kVariants[v];
-    int nt = round_up((Nmax + vi.ppt - 1) / vi.ppt, 32);
+    int nt = round_up((Nmax + vi.ppt - 1) / vi.ppt * vi.tpp, 32);
     nt = std::max(nt, 32);
     return nt <= vi.maxt ? nt : 0;
 }
 
-// Built-in choice of variant for state dimension d and Nmax particles.
-int pick_variant(int d, int Nmax) {
+// Built-in choice of variant for state dimension d, Nmax particles and B
+// sequences on an SM count of sms. Fewer sequences than SMs: one block per
+// sequence, so the step's latency decides, and splitting each particle's
+// sums over 8 (or 4) lanes shortens the serial chains.
+int pick_variant(int d, int Nmax, int B, int sms) {
+    if (d < 8 && B < sms) {
+        if (variant_threads(4, Nmax)) return 4;
+        if (variant_threads(5, Nmax)) return 5;
+    }
     if (d >= 8) return variant_threads(1, Nmax) ? 1 : 2;
     if (Nmax >= 128 && variant_threads(3, Nmax)) return 3;
     if (variant_threads(0, Nmax)) return 0;
@@ -299,7 +306,7 @@ smap_status cuda_fail(smap_handle* h, cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
     } while (0)
 
-int heuristic_variant(const smap_handle* h) { return pick_variant(h->d, h->Nmax); }
+int heuristic_variant(const smap_handle* h) { return pick_variant(h->d, h->Nmax, h->B, h->num_sms); }
 
 smap_status configure_kernel(smap_handle* h, const void* fn, size_t smem) {
     if (smem > h->max_smem)
@@ -630,10 +637,11 @@ smap_status smap_last_kernel_ms(smap_handle* h, float* seq_ms, float* batch_ms) 
 
 int smap_num_variants(void) { return kNumVariants; }
 
-smap_status smap_variant_info(int v, int* ppt, int* maxt) {
+smap_status smap_variant_info(int v, int* ppt, int* maxt, int* tpp) {
     if (v < 0 || v >= kNumVariants) return SMAP_E_INVAL;
     if (ppt) *ppt = kVariants[v].ppt;
     if (maxt) *maxt = kVariants[v].maxt;
+    if (tpp) *tpp = kVariants[v].tpp;
     return SMAP_OK;
 }
 

@@ -15,10 +15,14 @@ ModelKernels kernels_planar_arm7() {
     k.seq[1] = (const void*)seq_kernel<M, 2, 512, 1>;
     k.seq[2] = (const void*)seq_kernel<M, 4, 256, 1>;
     k.seq[3] = (const void*)seq_kernel<M, 2, 256, 4>;
+    k.seq[4] = (const void*)seq_kernel<M, 1, 1024, 1, 8>;
+    k.seq[5] = (const void*)seq_kernel<M, 1, 1024, 1, 4>;
     k.dbg[0] = (const void*)debug_svgd_kernel<M, 1, 1024, 1>;
     k.dbg[1] = (const void*)debug_svgd_kernel<M, 2, 512, 1>;
     k.dbg[2] = (const void*)debug_svgd_kernel<M, 4, 256, 1>;
     k.dbg[3] = (const void*)debug_svgd_kernel<M, 2, 256, 4>;
+    k.dbg[4] = (const void*)debug_svgd_kernel<M, 1, 1024, 1, 8>;
+    k.dbg[5] = (const void*)debug_svgd_kernel<M, 1, 1024, 1, 4>;
     k.pf[0] = (const void*)pf_seq_kernel<M, 1, 1024>;
     k.pf[1] = (const void*)pf_seq_kernel<M, 4, 1024>;
     return k;

@@ -10,12 +10,16 @@
 namespace smap {
 
 // Compiled variants of the step kernels: particles per thread, the block-size
-// bound given to the compiler, and the minimum resident blocks it targets.
+// bound given to the compiler, the minimum resident blocks it targets, and
+// threads per particle (the lanes that split one particle's sums over the
+// other particles: shorter serial chains when a sequence's block would
+// otherwise hold only a warp or two).
 struct VariantInfo {
-    int ppt, maxt, minb;
+    int ppt, maxt, minb, tpp;
 };
-constexpr int kNumVariants = 4;
-constexpr VariantInfo kVariants[kNumVariants] = {{1, 1024, 1}, {2, 512, 1}, {4, 256, 1}, {2, 256, 4}};
+constexpr int kNumVariants = 6;
+constexpr VariantInfo kVariants[kNumVariants] = {{1, 1024, 1, 1}, {2, 512, 1, 1}, {4, 256, 1, 1},
+                                                 {2, 256, 4, 1}, {1, 1024, 1, 8}, {1, 1024, 1, 4}};
 
 struct ModelKernels {
     int kind, D, DP;
@@ -66,7 +70,7 @@ extern std::atomic<uint64_t> g_launches;
 const ModelKernels* kernels_for(int kind);
 bool make_model(int kind, const double* p, int np, ModelParams& mp, std::string& err);
 int variant_threads(int v, int Nmax);
-int pick_variant(int d, int Nmax);
+int pick_variant(int d, int Nmax, int B, int sms);
 __global__ void backtrack_kernel(int B, int Nmax, int maxT, int d, const int* __restrict__ tcur,
                                  const int* __restrict__ Nseq, const double* __restrict__ phi,
                                  const uint16_t* __restrict__ psi, const float* __restrict__ hist,

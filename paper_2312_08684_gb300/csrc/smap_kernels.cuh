@@ -124,6 +124,15 @@ __device__ __forceinline__ float sqdist(const float* a, const float* b) {
     return s;
 }
 
+// Sum over the TPP consecutive lanes that share a particle (TPP divides 32;
+// every lane of the warp must call).
+template <int TPP>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+    for (int o = TPP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // ---------------------------------------------------------------------------
 // a3: exact median of the N(N-1)/2 squared distances.
 // ---------------------------------------------------------------------------
@@ -562,14 +571,15 @@ __device__ void prepare_step(const ModelParams& mp, const Sm& s, int t, int N, i
 // particles held as x^ = (x - c) * sc in xs; each particle is first rescaled
 // by `rescale` (the new kernel scale over the old) and written back. What is
 // stored is what the update needs: w_i = Aw g_i - Bw x^_i in gs and |x^_i|^2
-// in nrm (see rbf_update).
+// in nrm (see rbf_update). With TPP > 1 threads per particle, the lanes of a
+// group split the loop over the previous set and combine by shuffles.
 // ---------------------------------------------------------------------------
-template <class M, int PPT>
+template <class M, int PPT, int TPP = 1>
 __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const Sm& s, int N, int Np,
                                                   int prior, float rescale, float inv_sc, float Aw,
                                                   float Bw) {
     constexpr int D = M::D, DP = M::DP;
-    const int tid = threadIdx.x, NT = blockDim.x;
+    const int tid = threadIdx.x / TPP, NT = blockDim.x / TPP, r = threadIdx.x % TPP;
     float xt[PPT][D], A[PPT][D], S[PPT], Mref[PPT];
     float cf[D], qk[D];
 #pragma unroll
@@ -589,7 +599,8 @@ __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const S
             xt[p][c] = xh[c] * qk[c];
             A[p][c] = 0.0f;
         }
-        if (i < N) store_row<D, DP>(s.xs, i, xh);
+        if constexpr (TPP > 1) __syncwarp();   // the group has read the row before it is rewritten
+        if (i < N && r == 0) store_row<D, DP>(s.xs, i, xh);
         S[p] = 0.0f;
         // reference logit: the particle's own parent in the previous set
         float fr[D];
@@ -604,7 +615,7 @@ __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const S
         int bj[PPT];
 #pragma unroll
         for (int p = 0; p < PPT; ++p) { bv[p] = -INFINITY; bj[p] = 0; }
-        for (int j = 0; j < Np; ++j) {
+        for (int j = r; j < Np; j += TPP) {
             float fj[D];
             load_row<D, DP>(s.fs, j, fj);
             const float pj = s.phf[j];
@@ -618,6 +629,15 @@ __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const S
         }
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
+            if constexpr (TPP > 1) {
+                // best over the group's lanes, lowest j among equal scores
+#pragma unroll
+                for (int o = TPP / 2; o > 0; o >>= 1) {
+                    const float ov = __shfl_xor_sync(0xffffffffu, bv[p], o);
+                    const int oj = __shfl_xor_sync(0xffffffffu, bj[p], o);
+                    if (ov > bv[p] || (ov == bv[p] && oj < bj[p])) { bv[p] = ov; bj[p] = oj; }
+                }
+            }
             float fj[D];
             load_row<D, DP>(s.fs, bj[p], fj);
             S[p] = 1.0f;
@@ -629,7 +649,7 @@ __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const S
         // mixture responsibilities w_ij = 2^(Mref - |x~_i - f~_j|^2) / sum:
         // the parent's term is 1, so the sum is >= 1; a sum above 2^100 (a
         // far better component than the parent) is redone with the true max
-        for (int j = 0; j < Np; ++j) {
+        for (int j = r; j < Np; j += TPP) {
             float fj[D];
             load_row<D, DP>(s.fs, j, fj);
 #pragma unroll
@@ -648,17 +668,28 @@ __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const S
         }
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
-            if (!(S[p] <= 1.2676506e30f)) {   // 2^100, or NaN
+            if constexpr (TPP > 1) {
+                S[p] = group_sum<TPP>(S[p]);
+#pragma unroll
+                for (int c = 0; c < D; ++c) A[p][c] = group_sum<TPP>(A[p][c]);
+            }
+            const bool redo = !(S[p] <= 1.2676506e30f);   // 2^100, or NaN
+            // with TPP > 1 the redo path shuffles, so the whole warp enters it
+            if (TPP == 1 ? redo : __any_sync(0xffffffffu, redo)) {
                 float mn = INFINITY;
-                for (int j = 0; j < Np; ++j) {
+                for (int j = r; j < Np; j += TPP) {
                     float fj[D];
                     load_row<D, DP>(s.fs, j, fj);
                     mn = fminf(mn, sqdist<D>(xt[p], fj));
                 }
-                S[p] = 0.0f;
+                if constexpr (TPP > 1) {
 #pragma unroll
-                for (int c = 0; c < D; ++c) A[p][c] = 0.0f;
-                for (int j = 0; j < Np; ++j) {
+                    for (int o = TPP / 2; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+                }
+                float S2 = 0.0f, A2[D];
+#pragma unroll
+                for (int c = 0; c < D; ++c) A2[c] = 0.0f;
+                for (int j = r; j < Np; j += TPP) {
                     float fj[D], diff[D], m = -mn;
                     load_row<D, DP>(s.fs, j, fj);
 #pragma unroll
@@ -667,9 +698,19 @@ __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const S
                         m = fmaf(diff[c], diff[c], m);
                     }
                     const float e = fast_exp2(-m);
-                    S[p] += e;
+                    S2 += e;
 #pragma unroll
-                    for (int c = 0; c < D; ++c) A[p][c] = fmaf(e, diff[c], A[p][c]);
+                    for (int c = 0; c < D; ++c) A2[c] = fmaf(e, diff[c], A2[c]);
+                }
+                if constexpr (TPP > 1) {
+                    S2 = group_sum<TPP>(S2);
+#pragma unroll
+                    for (int c = 0; c < D; ++c) A2[c] = group_sum<TPP>(A2[c]);
+                }
+                if (redo) {
+                    S[p] = S2;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) A[p][c] = A2[c];
                 }
             }
         }
@@ -677,7 +718,7 @@ __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const S
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         const int i = tid + p * NT;
-        if (i >= N) continue;
+        if (i >= N || r != 0) continue;
         float x[D], g[D];
         float xh[D];
         load_row<D, DP>(s.xs, i, xh);
@@ -715,10 +756,10 @@ __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const S
 // distance is |x^_i|^2 + |x^_k|^2 - 2 x^_i . x^_k, well conditioned because the
 // coordinates are in units of the kernel width.
 // ---------------------------------------------------------------------------
-template <class M, int PPT>
+template <class M, int PPT, int TPP = 1>
 __device__ __forceinline__ void rbf_update(const Sm& s, int N, float Bc) {
     constexpr int D = M::D, DP = M::DP;
-    const int tid = threadIdx.x, NT = blockDim.x;
+    const int tid = threadIdx.x / TPP, NT = blockDim.x / TPP, r = threadIdx.x % TPP;
     float xi[PPT][D], ni[PPT], Sw[PPT][D], S0[PPT];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
@@ -733,7 +774,7 @@ __device__ __forceinline__ void rbf_update(const Sm& s, int N, float Bc) {
         }
     }
 #pragma unroll 2
-    for (int k = 0; k < N; ++k) {
+    for (int k = r; k < N; k += TPP) {
         float xk[D], wk[D];
         load_row<D, DP>(s.xs, k, xk);
         load_row<D, DP>(s.gs, k, wk);
@@ -749,11 +790,19 @@ __device__ __forceinline__ void rbf_update(const Sm& s, int N, float Bc) {
             for (int c = 0; c < D; ++c) Sw[p][c] = fmaf(kap, wk[c], Sw[p][c]);
         }
     }
+    if constexpr (TPP > 1) {
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            S0[p] = group_sum<TPP>(S0[p]);
+#pragma unroll
+            for (int c = 0; c < D; ++c) Sw[p][c] = group_sum<TPP>(Sw[p][c]);
+        }
+    }
     __syncthreads();   // every thread is done reading xs / gs / nrm
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         const int i = tid + p * NT;
-        if (i >= N) continue;
+        if (i >= N || r != 0) continue;
         const float cx = 0.5f * fmaf(Bc, S0[p], 1.0f);
         float xn[D];
 #pragma unroll
@@ -769,11 +818,11 @@ __device__ __forceinline__ void rbf_update(const Sm& s, int N, float Bc) {
 //   KER 2, Matern 3/2  kappa = (1 + s) e^-s, s = sqrt(3u), repulsion weight e^-s
 // The drive (gs = A g_k) and the repulsion Bk (x^_i sum rho - sum rho x^_k)
 // accumulate separately, their weights differing.
-template <class M, int PPT, int KER>
+template <class M, int PPT, int KER, int TPP = 1>
 __device__ __forceinline__ void kernel_update(const Sm& s, int N, float Bk) {
     constexpr int D = M::D, DP = M::DP;
     constexpr float kLn2 = 0.6931471805599453f;
-    const int tid = threadIdx.x, NT = blockDim.x;
+    const int tid = threadIdx.x / TPP, NT = blockDim.x / TPP, r = threadIdx.x % TPP;
     float xi[PPT][D], ni[PPT], Sg[PPT][D], Sx[PPT][D], Sr[PPT];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
@@ -789,7 +838,7 @@ __device__ __forceinline__ void kernel_update(const Sm& s, int N, float Bk) {
         }
     }
 #pragma unroll 2
-    for (int k = 0; k < N; ++k) {
+    for (int k = r; k < N; k += TPP) {
         float xk[D], gk[D];
         load_row<D, DP>(s.xs, k, xk);
         load_row<D, DP>(s.gs, k, gk);
@@ -817,11 +866,22 @@ __device__ __forceinline__ void kernel_update(const Sm& s, int N, float Bk) {
             }
         }
     }
+    if constexpr (TPP > 1) {
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            Sr[p] = group_sum<TPP>(Sr[p]);
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                Sg[p][c] = group_sum<TPP>(Sg[p][c]);
+                Sx[p][c] = group_sum<TPP>(Sx[p][c]);
+            }
+        }
+    }
     __syncthreads();   // every thread is done reading xs / gs / nrm
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         const int i = tid + p * NT;
-        if (i >= N) continue;
+        if (i >= N || r != 0) continue;
         float xn[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
@@ -835,7 +895,7 @@ __device__ __forceinline__ void kernel_update(const Sm& s, int N, float Bk) {
 
 // a3..a6: L iterations on the absolute particles in xs (left absolute on
 // return). hout (may be null) receives h per iteration.
-template <class M, int PPT>
+template <class M, int PPT, int TPP = 1>
 __device__ void svgd_iterations(const ModelParams& mp, const Sm& s, int N, int Np, int L, float eps,
                                 int bw_rule, float bw_value, int prior, MedState& st, float q_extra,
                                 float* hout, int* stats, int kernel) {
@@ -883,12 +943,12 @@ __device__ void svgd_iterations(const ModelParams& mp, const Sm& s, int N, int N
         const float Bc = 2.0f * eps / ((float)N * h);
         // RBF: the update is regrouped around w_k = A g_k - Bc x^_k; the
         // other kernels keep A g_k and add their repulsion separately
-        rescale_and_score<M, PPT>(mp, s, N, Np, prior, sc_new / sc, 1.0f / sc_new, A, kernel == 0 ? Bc : 0.0f);
+        rescale_and_score<M, PPT, TPP>(mp, s, N, Np, prior, sc_new / sc, 1.0f / sc_new, A, kernel == 0 ? Bc : 0.0f);
         sc = sc_new;
         __syncthreads();
-        if (kernel == 1) kernel_update<M, PPT, 1>(s, N, eps / ((float)N * h));
-        else if (kernel == 2) kernel_update<M, PPT, 2>(s, N, 3.0f * eps / ((float)N * h));
-        else rbf_update<M, PPT>(s, N, Bc);
+        if (kernel == 1) kernel_update<M, PPT, 1, TPP>(s, N, eps / ((float)N * h));
+        else if (kernel == 2) kernel_update<M, PPT, 2, TPP>(s, N, 3.0f * eps / ((float)N * h));
+        else rbf_update<M, PPT, TPP>(s, N, Bc);
     }
     // back to absolute coordinates
     const float inv = 1.0f / sc;
@@ -1069,7 +1129,7 @@ __device__ inline float init_spread(const ModelParams& mp) {
 // ---------------------------------------------------------------------------
 // The persistent sequence kernel.
 // ---------------------------------------------------------------------------
-template <class M, int PPT, int MAXT, int MINB>
+template <class M, int PPT, int MAXT, int MINB, int TPP = 1>
 __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__ SeqArgs a) {
     constexpr int D = M::D, DP = M::DP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1123,8 +1183,8 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
                                  a.seed, (uint32_t)b, xin);
             if (!a.viterbi_only) {
                 st.fresh = 1;
-                svgd_iterations<M, PPT>(mp, s, N, Np, a.L, a.eps, a.bw_rule, a.bw_value, a.prior, st,
-                                        q_extra, nullptr, a.stats, a.kernel);
+                svgd_iterations<M, PPT, TPP>(mp, s, N, Np, a.L, a.eps, a.bw_rule, a.bw_value, a.prior, st,
+                                             q_extra, nullptr, a.stats, a.kernel);
             }
             int best[PPT];
             double phinew[PPT];
@@ -1167,7 +1227,7 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
 }
 
 // Debug: n iterations of SVGD from given particles (one CTA per sequence).
-template <class M, int PPT, int MAXT, int MINB>
+template <class M, int PPT, int MAXT, int MINB, int TPP = 1>
 __global__ void __launch_bounds__(MAXT, MINB) debug_svgd_kernel(const __grid_constant__ DebugSvgdArgs a) {
     constexpr int D = M::D, DP = M::DP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1189,7 +1249,7 @@ __global__ void __launch_bounds__(MAXT, MINB) debug_svgd_kernel(const __grid_con
     st.trend = 1.0f;
     st.w = 0.004f;
     st.fresh = 1;
-    svgd_iterations<M, PPT>(a.mp, s, a.N, a.Np, a.iters, a.eps, a.bw_rule, a.bw_value, a.prior, st,
+    svgd_iterations<M, PPT, TPP>(a.mp, s, a.N, a.Np, a.iters, a.eps, a.bw_rule, a.bw_value, a.prior, st,
                             init_spread(a.mp), a.hout ? a.hout + (size_t)b * a.iters : nullptr, nullptr, a.kernel);
     for (int e = tid; e < a.N * D; e += NT)
         a.xout[(size_t)b * a.N * D + e] = s.xs[(e / D) * DP + (e % D)];

@@ -115,7 +115,7 @@ extern "C" smap_status smap_viterbi_noalloc(int model, const double* params, int
         base = g_noalloc_addr[dev];
     }
 
-    const int v = pick_variant(d, N);
+    const int v = pick_variant(d, N, B, 0);   // the recursion alone: no lane split (sms = 0)
     const int nt = variant_threads(v, N);
     const void* fn = K->seq[v];
     const size_t smem = smem_layout(N, K->DP).total;

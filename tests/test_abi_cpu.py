@@ -45,8 +45,8 @@ def test_host_only_calls(libpath):
     assert "non-finite" in abi.smap_status_string(6)
     assert abi.smap_num_variants() >= 1
     for v in range(abi.smap_num_variants()):
-        ppt, maxt = abi.smap_variant_info(v)
-        assert ppt >= 1 and maxt % 32 == 0
+        ppt, maxt, tpp = abi.smap_variant_info(v)
+        assert ppt >= 1 and maxt % 32 == 0 and tpp in (1, 2, 4, 8, 16, 32)
     with pytest.raises(abi.SmapError):
         abi.smap_variant_info(99)
     assert abi.smap_kernel_launches() == 0

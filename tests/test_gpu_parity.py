@@ -63,7 +63,8 @@ CASES = {
 SPREAD = {"ngm1d": 2.0, "range": 0.3, "clutter": 0.3, "arm": 0.02, "linear": 0.2, "range_zv": 0.2, "se2": 0.1}
 
 
-def _svgd_case(oracle, name, t, n_iters, prior=0, bw_rule=0, bw_value=1.0, N=None, kernel=0, phi_spread=None):
+def _svgd_case(oracle, name, t, n_iters, prior=0, bw_rule=0, bw_value=1.0, N=None, kernel=0, phi_spread=None,
+               variant=None):
     wl = CASES[name]()
     if N is not None:
         wl.N = N
@@ -86,6 +87,8 @@ def _svgd_case(oracle, name, t, n_iters, prior=0, bw_rule=0, bw_value=1.0, N=Non
     Np = xprev.shape[1]
     phi = None if phi_spread is None else phi_spread * rng.normal(0, 1, (B, Np))
     with Estimator.from_workload(wl) as est:
+        if variant is not None:
+            est.set_variant(variant)
         xg, hg = est.debug_svgd(t, xprev, xinit, y, n_iters, phi)
     for b in range(B):
         xo, ho = m.svgd_iters(prior, bw_rule, bw_value, t, y[b].astype(np.float64), fprev[b],
@@ -201,8 +204,10 @@ def test_viterbi_on_identical_particle_sets(oracle, name):
 
 
 # ------------------------------------------------------------ whole runs ----
-def _run_gpu(wl, **kw):
+def _run_gpu(wl, variant=None, **kw):
     with Estimator.from_workload(wl, **kw) as est:
+        if variant is not None:
+            est.set_variant(variant)
         path, J = est.run_batch(wl.y, wl.T, wl.Nseq)
         hist = est.history()
         psi = est.backpointers()
@@ -310,12 +315,15 @@ def test_uneven_particle_counts_match_oracle(oracle):
 
 
 def test_variants_agree_bitwise():
-    """Every compiled (particles per thread, block) variant runs the same
-    per-particle arithmetic in the same order (mixture prior)."""
+    """Every compiled (particles per thread, block) variant with one thread per
+    particle runs the same per-particle arithmetic in the same order (mixture
+    prior)."""
     wl = W.make_range_cv(B=3, T=8, N=64, L=4, dropout=None)
     outs = []
     with Estimator.from_workload(wl) as est:
         for v in range(abi.smap_num_variants()):
+            if abi.smap_variant_info(v)[2] != 1:
+                continue
             try:
                 est.set_variant(v)
             except abi.SmapError:
@@ -347,3 +355,37 @@ def test_bad_arguments_rejected():
             est.run_batch(wl.y, T=np.array([5, 1], np.int32))      # > max_T
         with pytest.raises(abi.SmapError):
             est.run_batch(wl.y, Nseq=np.array([17, 1], np.int32))  # > N
+
+
+def _lane_split_variants():
+    return [v for v in range(abi.smap_num_variants()) if abi.smap_variant_info(v)[2] > 1]
+
+
+@pytest.mark.parametrize("name", ["ngm1d", "range", "clutter", "linear", "range_zv", "se2"])
+@pytest.mark.parametrize("t", [1, 3])
+def test_lane_split_variants_one_iteration(oracle, name, t):
+    """Variants that split each particle's sums over 4 or 8 lanes: one SVGD
+    iteration against the oracle, with the mixture, mean-gradient and
+    MAP-conditioned priors and the IMQ / Matern kernels."""
+    for v in _lane_split_variants():
+        for kw in (dict(), dict(prior=1), dict(prior=2, phi_spread=3.0), dict(kernel=1), dict(kernel=2)):
+            if name == "clutter" and kw.get("prior") == 2:
+                continue
+            for b, xg, xo, hg, ho in _svgd_case(oracle, name, t, 1, variant=v, **kw):
+                assert np.allclose(hg, ho, rtol=1e-5), (v, kw, hg, ho)
+                assert rel_err(xg, xo) <= 1e-5, (name, t, v, kw, b, rel_err(xg, xo))
+
+
+@pytest.mark.parametrize("name", ["range", "range_zv", "ngm1d"])
+def test_lane_split_variants_full_run(oracle, name):
+    wl = {"range": lambda: W.make_range_cv(B=3, T=20, N=48, L=10, dropout=(6, 10)),
+          "range_zv": lambda: W.make_range_zv(B=2, T=30, N=40, L=20, blocked=((8, 10),)),
+          "ngm1d": lambda: W.make_ngm1d(B=2, T=25, N=20, L=30)}[name]()
+    for v in _lane_split_variants():
+        path, J, hist, psi = _run_gpu(wl, variant=v)
+        for b in range(wl.B):
+            T = int(wl.T[b])
+            ref = _run_oracle(oracle, wl, b)
+            assert rel_err(hist[b, :T], ref["hist"]) <= 1e-3, (v, b)
+            assert rel_err(path[b, : T + 1], ref["path"]) <= 1e-3, (v, b)
+            assert J[b] == pytest.approx(ref["J"], rel=1e-3), (v, b)
