@@ -2,6 +2,7 @@
 the Stein sets need far fewer particles, Section V-A, Table Ex1).
 
   python -m paper_2312_08684_gb300.pf_compare [--runs 50] [--T 100] [--scenario A|C]
+                                              [--only stein|pf] [--N n]
 
 Scenario A: Section V-A's constants (growth model, z = x^2/20 + r), 50 runs of
 100 steps. Scenario C: the range-only zero-velocity model of Section V-C
@@ -65,10 +66,14 @@ def main(argv=None):
     ap.add_argument("--runs", type=int, default=50)
     ap.add_argument("--T", type=int, default=None)
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--only", choices=["stein", "pf"], default=None, help="run the rows of one method")
+    ap.add_argument("--N", type=int, default=None, help="run the rows with this particle count")
     args = ap.parse_args(argv)
     T = args.T or (100 if args.scenario == "A" else 600)
     out = []
     for method, N, paper_rmse, paper_ms in ROWS[args.scenario]:
+        if (args.only and method != args.only) or (args.N and N != args.N):
+            continue
         wl1 = _workload(args.scenario, 1, T, N)
         with Estimator.from_workload(wl1) as est:
             t1, _ = _run(est, method, wl1.y, args.reps)
