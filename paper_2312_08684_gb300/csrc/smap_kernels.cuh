@@ -990,8 +990,19 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
                              int* best, double* phinew) {
     constexpr int D = M::D, DP = M::DP;
     const int tid = threadIdx.x, NT = blockDim.x;
-    // K u with u = 2^-24, K = 64: covers the FP32 errors of the screen.
-    const float Ku = 3.814697265625e-06f;
+    // Rounding allowance of the FP32 scores, u = 2^-24. With the exact scaled
+    // difference e* and the error D of the computed one (|D| <= 5u|x~| + u|f~|
+    // per coordinate: the FP32 centring, the FP32 scale, the FP32 copy of the
+    // FP64 mean), 2|e*||D| <= g u e*^2 + D^2 / (g u) for any g > 0; with
+    // g = 50 the computed distance m~ is within u (67 m~ + (|x~|^2 + |f~|^2))
+    // of the exact one (first order, d <= 14, the subtraction and the FMA
+    // chain included). In score units (kLam / 2 per unit of m~) the allowance
+    // below is u (128 m~ + 4 (|x~|^2 + |f~|^2)) kLam / 2, and 8u |phi~| for
+    // the FP32 copy of phi_{t-1}(j) - max and the two roundings of L and U (3u):
+    // at least 1.8x each bound.
+    const float Ku = 3.814697265625e-06f;    // 64 u: per unit of kLam m~
+    const float Kf = 1.1920928955078125e-07f; // 2 u: per unit of kLam (|x~|^2 + |f~|^2)
+    const float Kp = 4.76837158203125e-07f;   // 8 u: per unit of |phi~|
     double pmax = -INFINITY;
     for (int j = tid; j < Np; j += NT) pmax = fmax(pmax, s.phis[j]);
     pmax = block_max_d(pmax, s.redd);
@@ -1004,7 +1015,7 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
         float F = 0.0f;
 #pragma unroll
         for (int c = 0; c < D; ++c) F = fmaf(fr[c], fr[c], F);
-        const float B = Ku * (kLam * F + fabsf(ph)) +
+        const float B = Kf * kLam * F + Kp * fabsf(ph) +
                         (float)(4.4408920985006262e-16 * (fabs(s.phis[j]) + fabs(pmax)));
         ab[j] = make_float2(ph + B, ph - B);
     }
@@ -1027,7 +1038,7 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
             xc[p][c] = (xr[c] - cf[c]) * qk[c];
             X = fmaf(xc[p][c], xc[p][c], X);
         }
-        C[p] = Ku * kLam * X;
+        C[p] = Kf * kLam * X;
         Lmax[p] = -INFINITY;
     }
     const float cl = -(0.5f + Ku) * kLam, cu = -(0.5f - Ku) * kLam;
