@@ -567,6 +567,58 @@ __device__ void prepare_step(const ModelParams& mp, const Sm& s, int t, int N, i
 }
 
 // ---------------------------------------------------------------------------
+// MAP-conditioned prior: per particle the predecessor j maximising
+// phi_{t-1}(j) + log p(x_i | x_{t-1}^j), i.e. phf_j - |x~_i - f~_j|^2 in log2
+// units (FP32, lowest j on ties), from the particles in xs at scale 1/inv_sc.
+// The index goes to nrm (as an int) for rescale_and_score; a separate pass so
+// that the other priors' score code keeps its registers.
+// ---------------------------------------------------------------------------
+template <class M, int PPT, int TPP = 1>
+__device__ __noinline__ void mapcond_select(const ModelParams& mp, const Sm& s, int N, int Np, float inv_sc) {
+    constexpr int D = M::D, DP = M::DP;
+    const int tid = threadIdx.x / TPP, NT = blockDim.x / TPP, r = threadIdx.x % TPP;
+    float xt[PPT][D], bv[PPT];
+    int bj[PPT];
+    float qk[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) qk[c] = mp.sqrt_qinv_f[c] * kKm * inv_sc;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        float xh[D];
+        load_row<D, DP>(s.xs, min(tid + p * NT, N - 1), xh);
+#pragma unroll
+        for (int c = 0; c < D; ++c) xt[p][c] = xh[c] * qk[c];
+        bv[p] = -INFINITY;
+        bj[p] = 0;
+    }
+    for (int j = r; j < Np; j += TPP) {
+        float fj[D];
+        load_row<D, DP>(s.fs, j, fj);
+        const float pj = s.phf[j];
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            const float v = pj - sqdist<D>(xt[p], fj);
+            const bool nb = v > bv[p];
+            bv[p] = nb ? v : bv[p];
+            bj[p] = nb ? j : bj[p];
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        if constexpr (TPP > 1) {
+#pragma unroll
+            for (int o = TPP / 2; o > 0; o >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, bv[p], o);
+                const int oj = __shfl_xor_sync(0xffffffffu, bj[p], o);
+                if (ov > bv[p] || (ov == bv[p] && oj < bj[p])) { bv[p] = ov; bj[p] = oj; }
+            }
+        }
+        const int i = tid + p * NT;
+        if (i < N && r == 0) reinterpret_cast<int*>(s.nrm)[i] = bj[p];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // a4: scores g_i = grad log p(z_t | x_i) + grad log prior(x_i) for the block's
 // particles held as x^ = (x - c) * sc in xs; each particle is first rescaled
 // by `rescale` (the new kernel scale over the old) and written back. What is
@@ -608,38 +660,16 @@ __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const S
         Mref[p] = sqdist<D>(xt[p], fr);
     }
     if (prior == 2) {
-        // MAP-conditioned: the predecessor j maximising phi_{t-1}(j) + log
-        // p(x_i | x_{t-1}^j), i.e. phf_j - |x~_i - f~_j|^2 in log2 units (FP32,
-        // lowest j on ties); its transition alone gives the prior score
-        float bv[PPT];
-        int bj[PPT];
-#pragma unroll
-        for (int p = 0; p < PPT; ++p) { bv[p] = -INFINITY; bj[p] = 0; }
-        for (int j = r; j < Np; j += TPP) {
-            float fj[D];
-            load_row<D, DP>(s.fs, j, fj);
-            const float pj = s.phf[j];
-#pragma unroll
-            for (int p = 0; p < PPT; ++p) {
-                const float v = pj - sqdist<D>(xt[p], fj);
-                const bool nb = v > bv[p];
-                bv[p] = nb ? v : bv[p];
-                bj[p] = nb ? j : bj[p];
-            }
-        }
+        // MAP-conditioned: the predecessor chosen by mapcond_select (its index
+        // is parked in nrm, which is rewritten below); its transition alone
+        // gives the prior score
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
-            if constexpr (TPP > 1) {
-                // best over the group's lanes, lowest j among equal scores
-#pragma unroll
-                for (int o = TPP / 2; o > 0; o >>= 1) {
-                    const float ov = __shfl_xor_sync(0xffffffffu, bv[p], o);
-                    const int oj = __shfl_xor_sync(0xffffffffu, bj[p], o);
-                    if (ov > bv[p] || (ov == bv[p] && oj < bj[p])) { bv[p] = ov; bj[p] = oj; }
-                }
-            }
+            const int i = tid + p * NT;
+            int jb = i < N ? reinterpret_cast<const int*>(s.nrm)[i] : 0;
+            jb = min(max(jb, 0), Np - 1);
             float fj[D];
-            load_row<D, DP>(s.fs, bj[p], fj);
+            load_row<D, DP>(s.fs, jb, fj);
             S[p] = 1.0f;
 #pragma unroll
             for (int c = 0; c < D; ++c) A[p][c] = xt[p][c] - fj[c];
@@ -674,18 +704,41 @@ __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const S
                 for (int c = 0; c < D; ++c) A[p][c] = group_sum<TPP>(A[p][c]);
             }
             const bool redo = !(S[p] <= 1.2676506e30f);   // 2^100, or NaN
-            // with TPP > 1 the redo path shuffles, so the whole warp enters it
-            if (TPP == 1 ? redo : __any_sync(0xffffffffu, redo)) {
+            if constexpr (TPP == 1) {
+                if (redo) {
+                    float mn = INFINITY;
+                    for (int j = 0; j < Np; ++j) {
+                        float fj[D];
+                        load_row<D, DP>(s.fs, j, fj);
+                        mn = fminf(mn, sqdist<D>(xt[p], fj));
+                    }
+                    S[p] = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) A[p][c] = 0.0f;
+                    for (int j = 0; j < Np; ++j) {
+                        float fj[D], diff[D], m = -mn;
+                        load_row<D, DP>(s.fs, j, fj);
+#pragma unroll
+                        for (int c = 0; c < D; ++c) {
+                            diff[c] = xt[p][c] - fj[c];
+                            m = fmaf(diff[c], diff[c], m);
+                        }
+                        const float e = fast_exp2(-m);
+                        S[p] += e;
+#pragma unroll
+                        for (int c = 0; c < D; ++c) A[p][c] = fmaf(e, diff[c], A[p][c]);
+                    }
+                }
+            } else if (__any_sync(0xffffffffu, redo)) {
+                // the redo path shuffles, so the whole warp enters it
                 float mn = INFINITY;
                 for (int j = r; j < Np; j += TPP) {
                     float fj[D];
                     load_row<D, DP>(s.fs, j, fj);
                     mn = fminf(mn, sqdist<D>(xt[p], fj));
                 }
-                if constexpr (TPP > 1) {
 #pragma unroll
-                    for (int o = TPP / 2; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-                }
+                for (int o = TPP / 2; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
                 float S2 = 0.0f, A2[D];
 #pragma unroll
                 for (int c = 0; c < D; ++c) A2[c] = 0.0f;
@@ -702,11 +755,9 @@ __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const S
 #pragma unroll
                     for (int c = 0; c < D; ++c) A2[c] = fmaf(e, diff[c], A2[c]);
                 }
-                if constexpr (TPP > 1) {
-                    S2 = group_sum<TPP>(S2);
+                S2 = group_sum<TPP>(S2);
 #pragma unroll
-                    for (int c = 0; c < D; ++c) A2[c] = group_sum<TPP>(A2[c]);
-                }
+                for (int c = 0; c < D; ++c) A2[c] = group_sum<TPP>(A2[c]);
                 if (redo) {
                     S[p] = S2;
 #pragma unroll
@@ -715,6 +766,7 @@ __device__ __forceinline__ void rescale_and_score(const ModelParams& mp, const S
             }
         }
     }
+    if constexpr (TPP > 1) __syncwarp();   // the group has read nrm before lane 0 rewrites it
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         const int i = tid + p * NT;
@@ -943,6 +995,10 @@ __device__ void svgd_iterations(const ModelParams& mp, const Sm& s, int N, int N
         const float Bc = 2.0f * eps / ((float)N * h);
         // RBF: the update is regrouped around w_k = A g_k - Bc x^_k; the
         // other kernels keep A g_k and add their repulsion separately
+        if (prior == 2) {
+            mapcond_select<M, PPT, TPP>(mp, s, N, Np, 1.0f / sc);
+            __syncthreads();
+        }
         rescale_and_score<M, PPT, TPP>(mp, s, N, Np, prior, sc_new / sc, 1.0f / sc_new, A, kernel == 0 ? Bc : 0.0f);
         sc = sc_new;
         __syncthreads();
