@@ -571,10 +571,11 @@ __device__ void prepare_step(const ModelParams& mp, const Sm& s, int t, int N, i
 // phi_{t-1}(j) + log p(x_i | x_{t-1}^j), i.e. phf_j - |x~_i - f~_j|^2 in log2
 // units (FP32, lowest j on ties), from the particles in xs at scale 1/inv_sc.
 // The index goes to nrm (as an int) for rescale_and_score; a separate pass so
-// that the other priors' score code keeps its registers.
+// that the other priors' score code keeps its registers (for wide states a
+// called function: inlined, its live ranges still cost the kernel spills).
 // ---------------------------------------------------------------------------
 template <class M, int PPT, int TPP = 1>
-__device__ __noinline__ void mapcond_select(const ModelParams& mp, const Sm& s, int N, int Np, float inv_sc) {
+__device__ __forceinline__ void mapcond_select(const ModelParams& mp, const Sm& s, int N, int Np, float inv_sc) {
     constexpr int D = M::D, DP = M::DP;
     const int tid = threadIdx.x / TPP, NT = blockDim.x / TPP, r = threadIdx.x % TPP;
     float xt[PPT][D], bv[PPT];
@@ -616,6 +617,10 @@ __device__ __noinline__ void mapcond_select(const ModelParams& mp, const Sm& s, 
         const int i = tid + p * NT;
         if (i < N && r == 0) reinterpret_cast<int*>(s.nrm)[i] = bj[p];
     }
+}
+template <class M, int PPT, int TPP>
+__device__ __noinline__ void mapcond_select_call(const ModelParams& mp, const Sm& s, int N, int Np, float inv_sc) {
+    mapcond_select<M, PPT, TPP>(mp, s, N, Np, inv_sc);
 }
 
 // ---------------------------------------------------------------------------
@@ -996,7 +1001,8 @@ __device__ void svgd_iterations(const ModelParams& mp, const Sm& s, int N, int N
         // RBF: the update is regrouped around w_k = A g_k - Bc x^_k; the
         // other kernels keep A g_k and add their repulsion separately
         if (prior == 2) {
-            mapcond_select<M, PPT, TPP>(mp, s, N, Np, 1.0f / sc);
+            if constexpr (D >= 8) mapcond_select_call<M, PPT, TPP>(mp, s, N, Np, 1.0f / sc);
+            else mapcond_select<M, PPT, TPP>(mp, s, N, Np, 1.0f / sc);
             __syncthreads();
         }
         rescale_and_score<M, PPT, TPP>(mp, s, N, Np, prior, sc_new / sc, 1.0f / sc_new, A, kernel == 0 ? Bc : 0.0f);
