@@ -53,10 +53,11 @@ __device__ inline void draw_normals64(uint64_t seed, uint32_t seq, uint32_t t, u
             const double u1 = ((double)w[2 * h] + 0.5) * (1.0 / 4294967296.0);
             const double u2 = ((double)w[2 * h + 1] + 0.5) * (1.0 / 4294967296.0);
             const double rad = sqrt(-2.0 * log(u1));
-            const double ang = 6.283185307179586 * u2;
+            double sn, cs;
+            sincospi(2.0 * u2, &sn, &cs);   // the angle 2 pi u2 without a pi-sized range reduction
             const int k0 = 4 * b + 2 * h;
-            if (k0 < D) z[k0] = rad * cos(ang);
-            if (k0 + 1 < D) z[k0 + 1] = rad * sin(ang);
+            if (k0 < D) z[k0] = rad * cs;
+            if (k0 + 1 < D) z[k0 + 1] = rad * sn;
         }
     }
 }
@@ -158,11 +159,15 @@ __device__ void pf_prepare_step(const ModelParams& mp, const Sm& s, int t, int N
         const int chunk = (Np + NT - 1) / NT;
         const int j0 = min(tid * chunk, Np), j1 = min(j0 + chunk, Np);
         double part = 0.0;
-        for (int j = j0; j < j1; ++j) part += exp(lw[j] - mx);
+        for (int j = j0; j < j1; ++j) {
+            const double w = exp(lw[j] - mx);
+            cum[j] = w;
+            part += w;
+        }
         double tot;
         double run = block_exclusive_scan_d(part, s.redd, &tot);
         for (int j = j0; j < j1; ++j) {
-            run += exp(lw[j] - mx);
+            run += cum[j];
             cum[j] = run;
         }
         W = tot;
