@@ -104,10 +104,13 @@ def _svgd_case(oracle, name, t, n_iters, prior=0, bw_rule=0, bw_value=1.0, N=Non
         yield b, xg[b], xo, hg[b], ho
 
 
+@pytest.mark.parametrize("variant", [None, 3])
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("t", [1, 3])
-def test_one_svgd_iteration_matches_oracle(oracle, name, t):
-    for b, xg, xo, hg, ho in _svgd_case(oracle, name, t, 1):
+def test_one_svgd_iteration_matches_oracle(oracle, name, t, variant):
+    """variant None: the built-in choice (8 lanes per particle at these small
+    batches, one lane for the 14-D arm); 3: the bench's one-lane kernel."""
+    for b, xg, xo, hg, ho in _svgd_case(oracle, name, t, 1, variant=variant):
         assert np.allclose(hg, ho, rtol=1e-5), (hg, ho)
         assert rel_err(xg, xo) <= 1e-5, (name, t, b, rel_err(xg, xo))
 
@@ -118,12 +121,13 @@ def test_meangrad_prior_matches_oracle(oracle, name):
         assert rel_err(xg, xo) <= 1e-5
 
 
+@pytest.mark.parametrize("variant", [None, 3])
 @pytest.mark.parametrize("name", ["range", "linear", "ngm1d", "range_zv", "se2", "arm"])
 @pytest.mark.parametrize("t", [1, 3])
-def test_map_conditioned_prior_matches_oracle(oracle, name, t):
+def test_map_conditioned_prior_matches_oracle(oracle, name, t, variant):
     """MAP-conditioned prior: the best predecessor under phi_{t-1} + log
     transition; seeded previous scores with a spread of 3 nats."""
-    for b, xg, xo, hg, ho in _svgd_case(oracle, name, t, 1, prior=2, phi_spread=3.0):
+    for b, xg, xo, hg, ho in _svgd_case(oracle, name, t, 1, prior=2, phi_spread=3.0, variant=variant):
         assert rel_err(xg, xo) <= 1e-5, (name, t, b, rel_err(xg, xo))
 
 
@@ -229,14 +233,15 @@ def test_full_run_ngm1d_matches_oracle(oracle):
     assert J[0] == pytest.approx(ref["J"], rel=1e-3)
 
 
+@pytest.mark.parametrize("variant", [None, 3])
 @pytest.mark.parametrize("name", ["range", "clutter", "linear", "range_zv", "se2"])
-def test_full_run_small_matches_oracle(oracle, name):
+def test_full_run_small_matches_oracle(oracle, name, variant):
     wl = {"range": lambda: W.make_range_cv(B=3, T=25, N=64, L=10, dropout=(8, 14)),
           "clutter": lambda: W.make_clutter_cv(B=3, Tmin=10, Tmax=20, N=48, L=10),
           "linear": lambda: W.make_linear_gauss(B=3, T=15, N=40, L=20),
           "range_zv": lambda: W.make_range_zv(B=3, T=30, N=40, L=20, blocked=((8, 10),)),
           "se2": lambda: W.make_se2_rb(B=3, T=30, N=40, L=20)}[name]()
-    path, J, hist, psi = _run_gpu(wl)
+    path, J, hist, psi = _run_gpu(wl, variant=variant)
     for b in range(wl.B):
         T = int(wl.T[b])
         ref = _run_oracle(oracle, wl, b)
@@ -246,14 +251,15 @@ def test_full_run_small_matches_oracle(oracle, name):
         assert np.all(np.isnan(path[b, T + 1:]))
 
 
+@pytest.mark.parametrize("variant", [None, 3])
 @pytest.mark.parametrize("name", ["range", "linear", "range_zv", "ngm1d"])
-def test_map_conditioned_full_run_matches_oracle(oracle, name):
+def test_map_conditioned_full_run_matches_oracle(oracle, name, variant):
     wl = {"range": lambda: W.make_range_cv(B=3, T=20, N=48, L=10, dropout=(6, 10)),
           "linear": lambda: W.make_linear_gauss(B=3, T=15, N=40, L=20),
           "range_zv": lambda: W.make_range_zv(B=3, T=25, N=30, L=20, blocked=((8, 6),)),
           "ngm1d": lambda: W.make_ngm1d(B=3, T=20, N=20, L=30)}[name]()
     wl.prior = 2
-    path, J, hist, psi = _run_gpu(wl)
+    path, J, hist, psi = _run_gpu(wl, variant=variant)
     for b in range(wl.B):
         T = int(wl.T[b])
         ref = _run_oracle(oracle, wl, b)
