@@ -1,6 +1,7 @@
 """Range-only localisation without a motion prior (the paper's Section V-C form).
 
   python -m paper_2312_08684_gb300.scenario_c [--runs 64] [--T 600] [--prior 0|2]
+                                             [--N n] [--variant v]
 
 2-D position, zero-velocity random walk with Q = (alpha dt)^2 I = 0.01 I, range
 measurements to three anchors with sigma_z = 0.5, anchor 1 blocked for six
@@ -40,7 +41,9 @@ def rmse_of(path, truth):
     return float(np.mean(np.sqrt(np.mean(np.sum(err ** 2, axis=2), axis=1))))
 
 
-def _timed(est, y, reps):
+def _timed(est, y, reps, variant=None):
+    if variant is not None:
+        est.set_variant(variant)
     est.run_batch(y)                                   # warm-up (graph capture, first launch)
     best = float("inf")
     for _ in range(reps):
@@ -56,16 +59,23 @@ def main(argv=None):
     ap.add_argument("--T", type=int, default=600)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--prior", type=int, default=W.PRIOR_MIXTURE, choices=[0, 1, 2])
+    ap.add_argument("--N", type=int, default=None, help="run only this particle count")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="step-kernel variant (smap_set_variant; default: the built-in choice)")
     args = ap.parse_args(argv)
     out = []
     for N, (paper_rmse, paper_ms) in PAPER.items():
+        if args.N and N != args.N:
+            continue
         wl1 = W.make_range_zv(B=1, T=args.T, N=N, prior=args.prior)
         with Estimator.from_workload(wl1) as est:
-            t1, _, _ = _timed(est, wl1.y, args.reps)
+            t1, _, _ = _timed(est, wl1.y, args.reps, args.variant)
+            variant = est.variant()
         wl = W.make_range_zv(B=args.runs, T=args.T, N=N, prior=args.prior)
         with Estimator.from_workload(wl) as est:
-            tb, path, J = _timed(est, wl.y, args.reps)
+            tb, path, J = _timed(est, wl.y, args.reps, args.variant)
         r = {"N": N, "L": wl.L, "T": args.T, "runs": args.runs, "prior": args.prior,
+             "variant_single": list(variant),
              "ms_per_step_single": 1e3 * t1 / args.T, "paper_ms_per_step": paper_ms,
              "seq_steps_per_s_batched": args.runs * args.T / tb,
              "rmse": rmse_of(path, wl.truth), "paper_rmse": paper_rmse,
