@@ -91,3 +91,31 @@ def test_pf_map_is_the_best_path_over_the_filter_supports(oracle, kind_name):
         path = np.vstack([wl.x0[0][None, :], res["hist"][np.arange(5), list(idx)]])
         best = max(best, m.path_score(path, z))
     assert res["J"] == pytest.approx(best, rel=1e-12)
+
+
+def test_pf_sets_have_near_tied_predecessors(oracle):
+    """Why the recursion needs FP64 on particle-filter sets: at N = 2000 the
+    filter samples the smooth maximum of phi_{t-1}(j) + log p(x_i | x_{t-1}^j)
+    densely, so the best and second-best predecessor of a particle are
+    typically 1e-6 nats apart, far below FP32's resolution of scores of
+    magnitude 10-100 (scenario A constants, exact FP64 scores)."""
+    wl = W.make_ngm1d(B=1, T=8, N=2000, paper_constants=True)
+    z = wl.y[0].astype(np.float64)
+    hist, _ = oracle.pf_sets(wl.kind, wl.params, 2000, wl.seed, 0, wl.x0[0], z)
+    a, b, c, om, toff, q, r, hc = wl.params
+    x = hist[:, :, 0]
+    ll = -0.5 * (z[:, :1] - hc * x * x) ** 2 / r - 0.5 * np.log(2 * np.pi * r)
+
+    def f(v, t):
+        return a * v + b * v / (1 + v * v) + c * np.cos(om * (t + toff))
+
+    phi = ll[0] - 0.5 * (x[0] - f(wl.x0[0, 0], 1)) ** 2 / q - 0.5 * np.log(2 * np.pi * q)
+    gaps = []
+    for t in range(2, 9):
+        S = phi[None, :] - 0.5 * (x[t - 1][:, None] - f(x[t - 2], t)[None, :]) ** 2 / q
+        srt = np.sort(S, axis=1)
+        gaps.append(srt[:, -1] - srt[:, -2])
+        phi = ll[t - 1] - 0.5 * np.log(2 * np.pi * q) + srt[:, -1]
+    gaps = np.concatenate(gaps)
+    assert np.median(gaps) < 1e-4
+    assert np.mean(gaps < 1e-4) > 0.5
