@@ -119,3 +119,19 @@ def test_pf_sets_have_near_tied_predecessors(oracle):
     gaps = np.concatenate(gaps)
     assert np.median(gaps) < 1e-4
     assert np.mean(gaps < 1e-4) > 0.5
+
+
+def test_pf_map_beats_every_filter_lineage(oracle):
+    """Every ancestral lineage of the filter is a path through its supports, so
+    its J (Theorem 1) cannot exceed the MAP sequence's."""
+    wl = W.make_range_cv(B=1, T=15, N=200, dropout=(4, 8))
+    z = wl.y[0].astype(np.float64)
+    res = oracle.pf_map_sequence(wl.kind, wl.params, 200, 4, 0, wl.x0[0], z)
+    m = oracle.Model(wl.kind, wl.params)
+    for i in range(0, 200, 17):
+        idx = [i]
+        for t in range(14, 0, -1):
+            idx.append(res["anc"][t, idx[-1]])
+        idx = idx[::-1]
+        path = np.vstack([wl.x0[0][None, :], res["hist"][np.arange(15), idx]])
+        assert m.path_score(path, z) <= res["J"] + 1e-9 * abs(res["J"])

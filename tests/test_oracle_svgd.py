@@ -167,3 +167,15 @@ def test_other_kernels_keep_the_mean_and_weight_the_drive(oracle, kernel):
     r_rbf, _ = m2.svgd_iters(0, 0, 1.0, 2, z, fprev, x1, 3, 0.002)
     r_k, _ = m2.svgd_iters(0, 0, 1.0, 2, z, fprev, x1, 3, 0.002, kernel=kernel)
     assert np.array_equal(r_rbf, r_k)
+
+
+def test_single_particle_priors_agree_over_a_run(oracle):
+    """With one particle every step's previous set has one member, so the
+    mixture, mean-gradient and MAP-conditioned priors give the same run."""
+    wl = W.make_range_cv(B=1, T=10, N=1, L=5)
+    z = wl.y[0].astype(np.float64)
+    runs = [oracle.run_sequence(wl.kind, wl.params, 1, wl.L, wl.step, wl.bw_rule, wl.bw_value, prior,
+                                wl.seed, 0, wl.x0[0], z) for prior in (0, 1, 2)]
+    for r in runs[1:]:
+        assert np.allclose(r["path"], runs[0]["path"], rtol=1e-13, atol=0)
+        assert r["J"] == pytest.approx(runs[0]["J"], rel=1e-13)
