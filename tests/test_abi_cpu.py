@@ -50,3 +50,19 @@ def test_host_only_calls(libpath):
     with pytest.raises(abi.SmapError):
         abi.smap_variant_info(99)
     assert abi.smap_kernel_launches() == 0
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/smap.h compiles as C99 with warnings as errors: plain types and
+    pointers only, usable from any language with a C FFI."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "smap.h"\n'
+                   "int main(void) { smap_config c = {0}; (void)c; return SMAP_OK; }\n")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        "-c", str(src), "-o", str(tmp_path / "use_header.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
