@@ -18,7 +18,7 @@
  *   4. Backtracking (Section IV-B, "Backtracking the MAP Sequence").
  * SVGD itself is Algorithm 1 with the empirical direction Eq. (svgd_iterate).
  *
- * Readings of points the paper leaves open (each is also listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - Kernel: RBF kappa(x,x') = exp(-||x-x'||^2 / h); the paper names the RBF
  *     kernel and the median heuristic (Section V, Table Ex6 caption) without a
  *     formula; h = s * med / log(N) with med the median of the squared pairwise
