@@ -45,7 +45,7 @@ typedef enum {
     SMAP_E_STATE = 4,        /* handle already failed, or call out of order */
     SMAP_E_TIMEOUT = 5,      /* a bounded device wait ran out */
     SMAP_E_NONFINITE = 6,    /* a particle or observation became NaN/Inf */
-    SMAP_E_UNSUPPORTED = 7   /* valid request this build does not implement */
+    SMAP_E_UNSUPPORTED = 7   /* valid request the library does not implement */
 } smap_status;
 
 /* Compiled-in scenario models. Parameter vectors (FP64), d and dy:
@@ -63,7 +63,7 @@ typedef enum {
  *  SMAP_MODEL_PLANAR_ARM   [dt, nl, r, q_0..q_{2nl-1}, len_0..len_{nl-1}] d=2nl, dy=2
  *      state (angles, rates), angles += dt * rates; z = sum_l len_l (cos th_l,
  *      sin th_l), th_l = sum_{m<=l} angle_m, noise N(0, r I) (Section V-D form;
- *      this build compiles nl = 7)
+ *      the library is compiled for nl = 7)
  *  SMAP_MODEL_LINEAR_GAUSS [dt, q0, q1, q2, q3, r]                     d=4, dy=2
  *      constant velocity, z = (px, py) + N(0, r I)
  *  SMAP_MODEL_RANGE_ZV2D   [q0, q1, r, nb, a0x, a0y, ...]               d=2, dy=nb (1..8)

@@ -147,7 +147,7 @@ bool make_model(int kind, const double* p, int np, ModelParams& mp, std::string&
     }
     case SMAP_MODEL_PLANAR_ARM: {
         const int nl = np >= 3 ? (int)p[1] : 0;
-        if (nl != 7 || np != 3 + 3 * nl) { err = "PLANAR_ARM: this build compiles nl = 7 (24 parameters)"; return false; }
+        if (nl != 7 || np != 3 + 3 * nl) { err = "PLANAR_ARM: the library is compiled for nl = 7 (24 parameters)"; return false; }
         if (!(p[2] > 0)) { err = "PLANAR_ARM: r must be > 0"; return false; }
         mp.d = 2 * nl; mp.dy = 2;
         for (int c = 0; c < 2 * nl; ++c) mp.q[c] = p[3 + c];

@@ -286,7 +286,7 @@ def make_range_zv(B=1, T=600, N=40, L=100, step=0.005, seed=6, blocked=ZV_BLOCKE
 
 # --------------------------------------------------------------- se2_rb ----
 # Four landmarks around the 10 m reference circle (the paper shows four but
-# gives no coordinates; these are this build's choice).
+# gives no coordinates; these positions are chosen here).
 SE2_LANDMARKS = np.array([[12.0, 12.0], [-12.0, 12.0], [-12.0, -12.0], [12.0, -12.0]])
 
 
