@@ -66,3 +66,15 @@ def test_header_is_plain_c(tmp_path):
     r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
                         "-c", str(src), "-o", str(tmp_path / "use_header.o")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_no_device_fails_loudly(libpath):
+    """Without a usable CUDA device the library refuses to create a handle
+    (an error status, no silent CPU path)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2312_08684_gb300 import _binding as abi, workloads as W
+    wl = W.make_linear_gauss(B=2, T=4, N=16, L=3)
+    with pytest.raises(abi.SmapError):
+        abi.smap_create(wl.kind, wl.params, wl.N, wl.L, wl.step, 0, 1.0, 0, 1, 2, 4, wl.x0, None, 0)
