@@ -229,7 +229,8 @@ smap_status smap_pf_run_batch(smap_handle* h, const float* y_all, const int* T_p
  * plus 8 B N (2 + d) bytes of scores and means) are rejected with
  * SMAP_E_INVAL and a message on stderr. The first call on a device looks up
  * the array's device address (set-up, once per device, with that device
- * current); make that first call before any stream capture. The call is
+ * current; done again in the new context after a device reset); make that
+ * first call before any stream capture. The call is
  * asynchronous on `stream` (cudaStream_t, NULL = legacy default stream) and
  * clears what it needs at the start of each call; every call shares the
  * array, so calls that overlap on the GPU (other streams or host threads)

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -20,6 +21,19 @@ using namespace smap;
 namespace smap {
 
 std::atomic<uint64_t> g_launches{0};
+
+namespace {
+std::mutex g_smem_attr_mu;
+}
+
+cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes) {
+    std::lock_guard<std::mutex> lock(g_smem_attr_mu);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 
 // ---------------------------------------------------------------------------
 // Backtracking (Section IV-B): one warp per sequence. i_T = argmax phi_T
@@ -266,7 +280,8 @@ struct smap_handle {
     cudaGraphExec_t graph = nullptr;
     int graph_variant = -2, graph_grid = 0, graph_threads = 0, graph_items = -1;
     int last_threads = 0, last_grid = 0;
-    bool configured[kNumVariants * 2] = {};
+    bool configured[kNumVariants * 2] = {};   // shared-memory carveout set
+    bool capturing = false;                    // inside smap_run_batch's stream capture
     // pinned staging of smap_step's inputs; step_done marks when they were consumed
     float* ystep_h = nullptr;
     uint8_t* active_h = nullptr;
@@ -311,19 +326,21 @@ int heuristic_variant(const smap_handle* h) { return pick_variant(h->d, h->Nmax,
 smap_status configure_kernel(smap_handle* h, const void* fn, size_t smem) {
     if (smem > h->max_smem)
         return fail(h, SMAP_E_UNSUPPORTED, "shared memory need exceeds the device limit for this N and d");
+    // inside a stream capture the caller raised the limit just before it began
+    // (smap_run_batch), and no call of this library ever lowers it
+    if (h->capturing) return SMAP_OK;
+    SMAP_CUDA(h, ensure_dynamic_smem(fn, smem));
     for (int k = 0; k < kNumVariants; ++k) {
         bool* flag = fn == h->K->seq[k] ? &h->configured[k] : fn == h->K->dbg[k] ? &h->configured[kNumVariants + k] : nullptr;
         if (!flag) continue;
         if (!*flag) {
-            SMAP_CUDA(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             // the whole unified L1 as shared memory: as many resident sequences as registers allow
             SMAP_CUDA(h, cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                                               (int)cudaSharedmemCarveoutMaxShared));
             *flag = true;
         }
-        return SMAP_OK;
+        break;
     }
-    SMAP_CUDA(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return SMAP_OK;
 }
 
@@ -886,7 +903,9 @@ smap_status smap_run_batch(smap_handle* h, const float* y_all, const int* T_per_
         cudaGraph_t g = nullptr;
         SMAP_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         const uint64_t before = g_launches.load();
+        h->capturing = true;
         smap_status cst = batch_device_work(h, v);
+        h->capturing = false;
         cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
         g_launches.store(before);   // capture records launches; they run at replay
         if (cst) {

@@ -67,6 +67,14 @@ int proposal_d(const smap_proposal* p);
 
 // Shared by the ABI translation units (defined in smap_api.cu).
 extern std::atomic<uint64_t> g_launches;
+// Raises the dynamic shared-memory limit of kernel `fn` on the current device
+// to at least `bytes`, and never lowers it: handles of different N and the
+// handle-free entry points launch the same kernel functions with different
+// sizes, and the limit is one per function and device. Reads the current limit
+// from the device each time (so it holds across a device reset) under one
+// process-wide mutex (so two threads cannot interleave a read and a lower
+// write). Not a stream operation.
+cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes);
 const ModelKernels* kernels_for(int kind);
 bool make_model(int kind, const double* p, int np, ModelParams& mp, std::string& err);
 int variant_threads(int v, int Nmax);

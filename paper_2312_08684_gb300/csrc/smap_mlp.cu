@@ -572,12 +572,7 @@ smap_status launch_forward(smap_proposal* p, const float* feat, const int* idx, 
         g_launches.fetch_add(1);
         return SMAP_OK;
     }
-    static bool configured = false;
-    if (!configured) {
-        PCUDA(p, cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)mlp_fwd_smem()));
-        configured = true;
-    }
+    PCUDA(p, ensure_dynamic_smem((const void*)mlp_forward_kernel, mlp_fwd_smem()));
     MlpFwdArgs a;
     memset(&a, 0, sizeof(a));
     a.W1 = p->W1b; a.W2 = p->W2b; a.W3 = p->W3b;

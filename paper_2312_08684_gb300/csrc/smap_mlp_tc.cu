@@ -31,6 +31,7 @@
 //   b1, b2, b3, normalisation, mbarriers, TMEM address
 #include <cuda_bf16.h>
 
+#include "smap_internal.h"
 #include "smap_mlp.cuh"
 #include "smap_tc.cuh"
 
@@ -421,13 +422,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_forward_tc_kernel(const __g
 size_t mlp_forward_tc_smem() { return kTcSmem; }
 
 cudaError_t mlp_forward_tc_launch(const MlpTcArgs& a, int num_sms, cudaStream_t st) {
-    static bool configured = false;
-    if (!configured) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    const cudaError_t e = ensure_dynamic_smem((const void*)mlp_forward_tc_kernel, kTcSmem);
+    if (e != cudaSuccess) return e;
     const long tiles = (a.rows + kTcRows - 1) / kTcRows;
     const int grid = (int)(tiles < num_sms ? (tiles > 0 ? tiles : 1) : num_sms);
     mlp_forward_tc_kernel<<<grid, kTcThreads, kTcSmem, st>>>(a);

@@ -16,6 +16,9 @@
 #include <mutex>
 #include <string>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "smap.h"
 #include "smap_internal.h"
 #include "smap_kernels.cuh"
@@ -28,10 +31,42 @@ namespace {
 constexpr size_t kNoallocScratchBytes = size_t(16) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-// Device address of g_noalloc_scratch per device, looked up once per device.
+// Device address of g_noalloc_scratch per device, looked up once per device
+// and context: a device reset creates a new context, in which the module (and
+// the array) may be loaded at another address, so the lookup is redone when
+// the current context's identity changes.
 std::mutex g_noalloc_mu;
 constexpr int kMaxDevices = 256;
-void* g_noalloc_addr[kMaxDevices] = {};
+struct ScratchAddr {
+    unsigned long long ctx = 0;   // cuCtxGetId of the context the address belongs to (0: none yet)
+    void* addr = nullptr;
+};
+ScratchAddr g_noalloc_addr[kMaxDevices];
+
+// Identity of the calling thread's current context, unique over the process's
+// lifetime (cuCtxGetId); 0 when no context is current or the driver entry
+// points are unavailable. The library links only the runtime, so the two
+// driver calls are reached through the runtime's entry-point lookup.
+unsigned long long current_context_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {   // called with g_noalloc_mu held
+        looked_up = true;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&get_cur, 4000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess)
+            get_cur = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&get_id, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess)
+            get_id = nullptr;
+    }
+    if (!get_cur || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_cur(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -102,17 +137,23 @@ extern "C" smap_status smap_viterbi_noalloc(int model, const double* params, int
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SMAP_E_CUDA;
     void* base = nullptr;
     {
-        // set-up, once per device, with that device current
+        // set-up, once per device (and again after a device reset), with that
+        // device current
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_addr[dev]) {
-            cudaError_t e = cudaGetSymbolAddress(&g_noalloc_addr[dev], g_noalloc_scratch);
+        ScratchAddr& sa = g_noalloc_addr[dev];
+        const unsigned long long ctx = current_context_id();
+        if (!sa.addr || ctx == 0 || ctx != sa.ctx) {
+            void* addr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
             if (e != cudaSuccess) {
-                g_noalloc_addr[dev] = nullptr;
+                sa = ScratchAddr();
                 std::fprintf(stderr, "smap_viterbi_noalloc: cudaGetSymbolAddress: %s\n", cudaGetErrorString(e));
                 return SMAP_E_CUDA;
             }
+            sa.addr = addr;
+            sa.ctx = current_context_id();   // the lookup made the primary context current if none was
         }
-        base = g_noalloc_addr[dev];
+        base = sa.addr;
     }
 
     const int v = pick_variant(d, N, B, 0);   // the recursion alone: no lane split (sms = 0)
@@ -124,8 +165,8 @@ extern "C" smap_status smap_viterbi_noalloc(int model, const double* params, int
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return SMAP_E_CUDA;
     if (!nt || smem > (size_t)smem_optin) return reject("N too large for shared memory at this state dimension");
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return SMAP_E_CUDA;
+    // raise, never lower: live handles launch the same kernel with larger sizes
+    if (ensure_dynamic_smem(fn, smem) != cudaSuccess) return SMAP_E_CUDA;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nt, smem) != cudaSuccess || occ < 1)
         return SMAP_E_CUDA;
@@ -140,8 +181,15 @@ extern "C" smap_status smap_viterbi_noalloc(int model, const double* params, int
     }
 
     cudaStream_t st = (cudaStream_t)stream;
+    auto launch_failed = [](cudaError_t e) {
+        std::fprintf(stderr, "smap_viterbi_noalloc: %s\n", cudaGetErrorString(e));
+        return SMAP_E_CUDA;
+    };
     noalloc_init_kernel<<<(B + kStatusExtra + 255) / 256, 256, 0, st>>>(B, N, T, c.tcur, c.Nseq, c.Tend, c.status,
                                                              c.queue, c.bwguess);
+    g_launches.fetch_add(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return launch_failed(e);
     SeqArgs a;
     memset(&a, 0, sizeof(a));
     a.mp = mp;
@@ -164,14 +212,15 @@ extern "C" smap_status smap_viterbi_noalloc(int model, const double* params, int
     a.stats = c.status + B;
     a.queue = c.queue;
     void* args[] = {&a};
-    cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, smem, st);
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, smem, st);
+    if (e != cudaSuccess) return launch_failed(e);
+    g_launches.fetch_add(1);
+    // backtracking reads what the recursion wrote: enqueued only after that
+    // launch was accepted
     backtrack_kernel<<<(B + 3) / 4, 128, 0, st>>>(B, N, T, d, c.tcur, c.Nseq, c.phi, c.psi, hist, x0,
                                                   c.status, c.idx, path, J);
-    g_launches.fetch_add(3);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        std::fprintf(stderr, "smap_viterbi_noalloc: %s\n", cudaGetErrorString(e));
-        return SMAP_E_CUDA;
-    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return launch_failed(e);
+    g_launches.fetch_add(1);
     return SMAP_OK;
 }
