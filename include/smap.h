@@ -297,6 +297,16 @@ const char* smap_proposal_last_error(const smap_proposal* p);
 smap_status smap_proposal_capture(smap_proposal* p, smap_handle* h, float* feat, float* targ, long max_rows,
                                   long* rows);
 
+/* Debug / parity: one inference forward like smap_proposal_forward, with
+ * `wait_ns` nanoseconds (global timer) as the limit of every bounded wait of
+ * the tensor-core kernel instead of the default 2 s. stall = 1 makes the
+ * MMA-issuing thread first wait on a barrier that nothing completes, so that
+ * wait runs out before any MMA is issued and the kernel's give-up path runs
+ * (the other warps' waits then run out too). Returns SMAP_E_TIMEOUT when a
+ * wait ran out (disp not written); the proposal stays usable. */
+smap_status smap_debug_proposal_forward(smap_proposal* p, const float* feat, long rows, float* disp,
+                                        uint64_t wait_ns, int stall);
+
 /* Attaches a proposal to a handle (p = NULL detaches): smap_run_batch then
  * initialises each step from u + MLP(u, z_t) and runs L_learned SVGD
  * iterations, one graph-captured launch sequence per time step. The proposal
@@ -349,11 +359,22 @@ smap_status smap_debug_normals(uint64_t seed, uint32_t seq, uint32_t t, uint32_t
  * reset, step kernel, backtracking). Either pointer may be NULL. */
 smap_status smap_last_kernel_ms(smap_handle* h, float* seq_kernel_ms, float* batch_ms);
 
-/* How the exact median of the bandwidth rule was found since the last reset
- * or batched run, summed over SVGD iterations: counts[0] by the bracket around
- * the previous median, counts[1] by the log-histogram locate (new step),
- * counts[2] by the radix-select fallback. Synchronises the stream. */
+/* How the exact median of the bandwidth rule was found since the last reset,
+ * batched run or smap_debug_svgd call, summed over SVGD iterations (counts:
+ * host [4]): counts[0] by the bracket around the previous median, counts[1]
+ * by the log-histogram locate (new step, or a bracket that held too many
+ * keys), counts[2] by the radix-select fallback, counts[3] how many of
+ * counts[1] needed the second, refining histogram (more than 2048 keys in the
+ * located bins). Synchronises the stream. */
 smap_status smap_debug_median_stats(smap_handle* h, int* counts);
+
+/* Debug / parity: while xinit_all is set (device [B][max_T][N][d] FP32, owned
+ * by the caller and alive while it is set), smap_run_batch with a proposal
+ * attached also copies every step's initial particles x^(0) = u + MLP(u, z_t)
+ * into row [b][t-1] (rows of steps a sequence does not run hold what the
+ * network computed for them). NULL stops the recording. Either change
+ * re-records the batched run's graph at its next call. */
+smap_status smap_debug_record_learned_init(smap_handle* h, float* xinit_all);
 
 /* Kernel launches the library has issued since load (its own kernels only). */
 uint64_t smap_kernel_launches(void);

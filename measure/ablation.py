@@ -1,6 +1,6 @@
 """Kernel / bandwidth / particle-count ablation on the paper's scenario A.
 
-  python -m paper_2312_08684_gb300.ablation [--runs 50] [--T 100]
+  python -m measure.ablation [--runs 50] [--T 100]
 
 Scenario A with the constants of Section V-A (growth model, z = x^2/20 + r,
 v ~ N(0,5), r ~ N(0,16), x_0 ~ N(0,5)), SVGD step 0.005, 100 iterations per
@@ -18,7 +18,7 @@ import json
 
 import numpy as np
 
-from . import Estimator, workloads as W
+from paper_2312_08684_gb300 import Estimator, workloads as W
 
 # (kernel, bandwidth scale, N) -> the paper's RMSE (Table Ex6)
 ROWS = [

@@ -1,7 +1,7 @@
 """Stein-MAP-Seq against PF-MAP-Seq on the same GPU (the paper's claim that
 the Stein sets need far fewer particles, Section V-A, Table Ex1).
 
-  python -m paper_2312_08684_gb300.pf_compare [--runs 50] [--T 100] [--scenario A|C]
+  python -m measure.pf_compare [--runs 50] [--T 100] [--scenario A|C]
                                               [--only stein|pf] [--N n]
 
 Scenario A: Section V-A's constants (growth model, z = x^2/20 + r), 50 runs of
@@ -27,7 +27,7 @@ import time
 
 import numpy as np
 
-from . import Estimator, workloads as W
+from paper_2312_08684_gb300 import Estimator, workloads as W
 
 ROWS = {
     "A": [("stein", 10, 2.0462, None), ("stein", 20, 2.1447, None), ("stein", 40, 2.2761, None),

@@ -1,6 +1,6 @@
 """Range-only localisation without a motion prior (the paper's Section V-C form).
 
-  python -m paper_2312_08684_gb300.scenario_c [--runs 64] [--T 600] [--prior 0|2]
+  python -m measure.scenario_c [--runs 64] [--T 600] [--prior 0|2]
                                              [--N n] [--variant v]
 
 2-D position, zero-velocity random walk with Q = (alpha dt)^2 I = 0.01 I, range
@@ -30,7 +30,7 @@ import time
 
 import numpy as np
 
-from . import Estimator, workloads as W
+from paper_2312_08684_gb300 import Estimator, workloads as W
 
 # N -> (the paper's Stein-MAP-Seq RMSE in m, its computation time in ms)
 PAPER = {20: (0.1722, 10.82), 30: (0.1442, 13.60), 40: (0.1369, 16.44)}

@@ -34,7 +34,7 @@ EXPORTS = [
     "smap_proposal_create", "smap_proposal_destroy", "smap_proposal_dims", "smap_proposal_get_weights",
     "smap_proposal_set_weights", "smap_proposal_fit_normalization", "smap_proposal_forward",
     "smap_proposal_loss_grad", "smap_proposal_train", "smap_proposal_last_error", "smap_proposal_capture",
-    "smap_set_proposal", "smap_pf_run_batch",
+    "smap_set_proposal", "smap_pf_run_batch", "smap_debug_proposal_forward", "smap_debug_record_learned_init",
 ]
 MLP_IN_P, MLP_OUT_P, MLP_H = 32, 16, 256
 
@@ -114,6 +114,8 @@ def load():
     L.smap_proposal_last_error.restype = ctypes.c_char_p
     L.smap_proposal_capture.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_long, ctypes.POINTER(ctypes.c_long)]
     L.smap_set_proposal.argtypes = [_VP, _VP, _I]
+    L.smap_debug_proposal_forward.argtypes = [_VP, _VP, ctypes.c_long, _VP, ctypes.c_uint64, _I]
+    L.smap_debug_record_learned_init.argtypes = [_VP, _VP]
     L.smap_viterbi_noalloc.argtypes = [_I, ctypes.POINTER(ctypes.c_double), _I, _I, _I, _I,
                                        _VP, _VP, _VP, _VP, _VP, _VP]
     L.smap_kernel_launches.argtypes = []
@@ -356,8 +358,9 @@ def smap_last_kernel_ms(h):
 
 
 def smap_debug_median_stats(h):
-    """(bracket hits, histogram locates, radix fallbacks) since the last reset / batched run."""
-    out = np.zeros(3, np.int32)
+    """(bracket hits, histogram locates, radix fallbacks, refined locates) since the last reset,
+    batched run or debug SVGD call."""
+    out = np.zeros(4, np.int32)
     _check(load().smap_debug_median_stats(h, ctypes.c_void_p(out.ctypes.data)), h)
     return tuple(int(v) for v in out)
 
@@ -420,6 +423,11 @@ def smap_proposal_forward(p, feat, disp):
     _pcheck(load().smap_proposal_forward(p, _dev(feat, np.float32), int(feat.shape[0]), _dev(disp, np.float32)), p)
 
 
+def smap_debug_proposal_forward(p, feat, disp, wait_ns, stall=0):
+    _pcheck(load().smap_debug_proposal_forward(p, _dev(feat, np.float32), int(feat.shape[0]),
+                                               _dev(disp, np.float32), int(wait_ns), int(stall)), p)
+
+
 def smap_proposal_loss_grad(p, feat, targ):
     n = smap_proposal_dims(p)[3]
     g = np.empty(n, np.float32)
@@ -450,6 +458,12 @@ def smap_proposal_capture(p, h, feat, targ):
 
 def smap_set_proposal(h, p, L_learned):
     _check(load().smap_set_proposal(h, p, int(L_learned)), h)
+
+
+def smap_debug_record_learned_init(h, xinit_all=None):
+    """xinit_all: CUDA tensor [B][max_T][N][d] float32, or None to stop recording."""
+    ptr = None if xinit_all is None else _dev(xinit_all, np.float32)
+    _check(load().smap_debug_record_learned_init(h, ptr), h)
 
 
 def smap_kernel_launches():

@@ -294,6 +294,7 @@ struct smap_handle {
     float* lu = nullptr;       // [B][Nmax][d]
     float* lxinit = nullptr;   // [B][Nmax][d]
     cudaStream_t side = nullptr;   // second chain of the learned launches
+    float* dbg_init = nullptr;     // debug: every step's learned initial particles [B][maxT][Nmax][d]
     // PF-MAP-Seq state (allocated by the first smap_pf_run_batch)
     double* pf_x64 = nullptr;  // [B][Nmax][d]
     double* pf_lw = nullptr;   // [B][Nmax]
@@ -444,8 +445,8 @@ smap_status collect_status(smap_handle* h) {
     std::vector<int> st(h->B + kStatusExtra);
     SMAP_CUDA(h, cudaMemcpyAsync(st.data(), h->status, sizeof(int) * st.size(), cudaMemcpyDeviceToHost, h->stream));
     SMAP_CUDA(h, cudaStreamSynchronize(h->stream));
-    if (st[h->B + 3] != 0)
-        return fail(h, SMAP_E_CUDA, "learned proposal: the tensor-core network kernel gave up a wait");
+    if (st[h->B + 4] != 0)
+        return fail(h, SMAP_E_TIMEOUT, "learned proposal: a bounded wait of the tensor-core network kernel ran out");
     for (int b = 0; b < h->B; ++b) {
         if (st[b] == SMAP_E_NONFINITE)
             return fail(h, SMAP_E_NONFINITE, "sequence " + std::to_string(b) + ": particles or scores became non-finite");
@@ -519,7 +520,7 @@ smap_status batch_device_work(smap_handle* h, int v) {
             ra.x0 = h->x0; ra.hist = h->hist; ra.y = h->y;
             ra.tcur = h->tcur; ra.Tend = h->Tend; ra.Nseq = h->Nseq;
             ra.feat = h->lfeat + r0 * 32; ra.u = h->lu + r0 * h->d;
-            ra.err = h->status + h->B + 3;
+            ra.err = h->status + h->B + 4;
             StepOpts so;
             so.xinit = h->lxinit;
             so.y_full = 1;
@@ -532,6 +533,12 @@ smap_status batch_device_work(smap_handle* h, int v) {
             for (int t = 1; t <= h->maxT; ++t) {
                 st = proposal_launch_init(h->prop, ra, h->lxinit + r0 * h->d, cs);
                 if (st) return fail(h, st, smap_proposal_last_error(h->prop));
+                if (h->dbg_init) {
+                    const size_t row = sizeof(float) * (size_t)h->Nmax * h->d;
+                    SMAP_CUDA(h, cudaMemcpy2DAsync(h->dbg_init + ((size_t)b0 * h->maxT + (t - 1)) * h->Nmax * h->d,
+                                                   row * h->maxT, h->lxinit + r0 * h->d, row, row, b1 - b0,
+                                                   cudaMemcpyDeviceToDevice, cs));
+                }
                 st = launch_seq(h, v, b1 - b0, 1, h->y, 0, nullptr, nullptr, nullptr, so);
                 if (st) return st;
             }
@@ -598,6 +605,17 @@ smap_status smap_set_proposal(smap_handle* h, smap_proposal* p, int L_learned) {
     return SMAP_OK;
 }
 
+smap_status smap_debug_record_learned_init(smap_handle* h, float* xinit_all) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    h->dbg_init = xinit_all;
+    if (h->graph) {   // the device work changes: record a new graph
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    return SMAP_OK;
+}
+
 smap_status smap_proposal_capture(smap_proposal* p, smap_handle* h, float* feat, float* targ, long max_rows,
                                   long* rows) {
     smap_status st = check_usable(h);
@@ -637,7 +655,7 @@ smap_status smap_debug_median_stats(smap_handle* h, int* counts) {
     smap_status st = check_usable(h);
     if (st) return st;
     if (!counts) return fail(h, SMAP_E_INVAL, "null output");
-    SMAP_CUDA(h, cudaMemcpyAsync(counts, h->status + h->B, sizeof(int) * 3, cudaMemcpyDeviceToHost, h->stream));
+    SMAP_CUDA(h, cudaMemcpyAsync(counts, h->status + h->B, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
     SMAP_CUDA(h, cudaStreamSynchronize(h->stream));
     return SMAP_OK;
 }
@@ -1132,6 +1150,9 @@ smap_status smap_debug_svgd(smap_handle* h, int t, const float* x_prev, int n_pr
     a.eps = (float)h->cfg.step; a.bw_value = (float)h->cfg.bw_value;
     a.xprev = dxp; a.x0 = h->x0; a.xinit = dxi; a.y = dy; a.xout = dxo; a.hout = dho; a.f64 = df;
     a.phiprev = dph;
+    a.stats = h->status + h->B;   // the median counters count this call alone
+    e = cudaMemsetAsync(a.stats, 0, sizeof(int) * 4, h->stream);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(h, e, "debug_svgd"); }
     const int v = h->variant >= 0 ? h->variant : heuristic_variant(h);
     const int nt = variant_threads(v, h->Nmax);
     const size_t smem = smem_layout(h->Nmax, h->K->DP).total;

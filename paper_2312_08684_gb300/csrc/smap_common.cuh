@@ -11,7 +11,7 @@ constexpr int kMaxParams = 128;  // model parameter vector length
 constexpr int kMaxDy = 64;       // largest observation dimension
 constexpr int kCandCap = 2048;   // median bracket candidates kept in shared memory
 constexpr int kMaxN = 4096;      // particles per sequence (backpointers are uint16)
-constexpr int kStatusExtra = 4;  // counters after the B per-sequence status words
+constexpr int kStatusExtra = 5;  // after the B per-sequence status words: 4 median counters, 1 error word
 
 // Model constants, passed by value in the kernel parameters (constant bank).
 struct ModelParams {
@@ -73,6 +73,7 @@ struct DebugSvgdArgs {
     double* f64;              // [B][Np][d] scratch
     const double* phiprev;    // [B][Np] previous scores (MAP-conditioned prior), or null = zeros
     int kernel;               // Stein kernel: 0 RBF, 1 IMQ, 2 Matern 3/2
+    int* stats;               // median-path counters [4] (see median_sqdist), or null
 };
 
 // ex2.approx: 2^x on the special-function unit (max rel. error ~2^-22).

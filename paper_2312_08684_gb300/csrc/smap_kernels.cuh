@@ -399,7 +399,8 @@ __device__ bool refine_pass(const Sm& s, int N, uint32_t lo, uint32_t hi, int r1
 // histogram over +-4 octaves of a guess locates the middle ranks (and a second
 // histogram over the located bins when they hold more than kCandCap keys); an
 // exact radix select is the last resort. stats (may be null): [0] bracket
-// hits, [1] histogram locates, [2] radix fallbacks.
+// hits, [1] histogram locates, [2] radix fallbacks, [3] of [1], those that
+// needed the refining second histogram.
 template <int D, int DP>
 __device__ float median_sqdist(const Sm& s, int N, float s2, float q_extra, MedState& st, int* stats) {
     const int P = N * (N - 1) / 2;
@@ -418,6 +419,7 @@ __device__ float median_sqdist(const Sm& s, int N, float s2, float q_extra, MedS
     __syncthreads();
     uint32_t v1 = 0, v2 = 0;
     int nc = 0, path = 2;
+    bool refined = false;     // the located keys needed the second, refining histogram
     float width = 0.0f;       // key-value width of the bracket that succeeded
     bool done = false;
     if (st.have && !st.fresh) {
@@ -430,7 +432,7 @@ __device__ float median_sqdist(const Sm& s, int N, float s2, float q_extra, MedS
         } else if (nc > kCandCap && s.redi[39]) {
             // the middle ranks are inside but the bracket is too wide
             done = refine_pass<D, DP>(s, N, __float_as_uint(lo), __float_as_uint(hi), r1, r2, v1, v2, nc, width);
-            if (done) path = 1;
+            if (done) { path = 1; refined = true; }
         }
     }
     if (!done) {
@@ -465,6 +467,7 @@ __device__ float median_sqdist(const Sm& s, int N, float s2, float q_extra, MedS
                     width = __uint_as_float(hi) - __uint_as_float(lo);
                 } else {
                     done = refine_pass<D, DP>(s, N, lo, hi, r1, r2, v1, v2, nc, width);
+                    refined = done;
                 }
                 if (done) path = 1;
             }
@@ -474,7 +477,10 @@ __device__ float median_sqdist(const Sm& s, int N, float s2, float q_extra, MedS
         v1 = radix_select<D, DP>(s, N, r1);
         v2 = (r2 == r1) ? v1 : radix_select<D, DP>(s, N, r2);
     }
-    if (stats && threadIdx.x == 0) atomicAdd(&stats[path], 1);
+    if (stats && threadIdx.x == 0) {
+        atomicAdd(&stats[path], 1);
+        if (refined) atomicAdd(&stats[3], 1);
+    }
     const float med_s = 0.5f * (__uint_as_float(v1) + __uint_as_float(v2));
     const float med = med_s / s2;
     if (st.have && !st.fresh && st.med > 0.0f) st.trend = fminf(fmaxf(med / st.med, 0.8f), 1.25f);
@@ -1179,6 +1185,12 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
                 const double sv = s.phis[j] + lt;
                 if (sv > bs[p]) { bs[p] = sv; blt[p] = lt; best[p] = j; }
             }
+            if (bs[p] == -INFINITY) {
+                // no finite candidate at all: predecessor 0, scored with its
+                // own (non-finite) transition term, so the score is not finite
+                best[p] = 0;
+                blt[p] = mp.logtrans_c - 0.5 * trans_m64<D>(mp, s.xs + row[p], f64);
+            }
         }
     }
 #pragma unroll
@@ -1323,7 +1335,7 @@ __global__ void __launch_bounds__(MAXT, MINB) debug_svgd_kernel(const __grid_con
     st.w = 0.004f;
     st.fresh = 1;
     svgd_iterations<M, PPT, TPP>(a.mp, s, a.N, a.Np, a.iters, a.eps, a.bw_rule, a.bw_value, a.prior, st,
-                            init_spread(a.mp), a.hout ? a.hout + (size_t)b * a.iters : nullptr, nullptr, a.kernel);
+                            init_spread(a.mp), a.hout ? a.hout + (size_t)b * a.iters : nullptr, a.stats, a.kernel);
     for (int e = tid; e < a.N * D; e += NT)
         a.xout[(size_t)b * a.N * D + e] = s.xs[(e / D) * DP + (e % D)];
 }

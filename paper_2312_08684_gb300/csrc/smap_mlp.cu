@@ -556,7 +556,8 @@ int num_sms() {
 // training passes keep the mma.sync kernel, which also writes the layer
 // activations that the backward pass reads.
 smap_status launch_forward(smap_proposal* p, const float* feat, const int* idx, long rows, bool train,
-                           const float* u, float* xout, cudaStream_t st, int* err = nullptr) {
+                           const float* u, float* xout, cudaStream_t st, int* err = nullptr,
+                           uint64_t wait_ns = kTcWaitNs, int stall = 0) {
     if (!train && !idx && xout) {
         MlpTcArgs t;
         t.W1 = p->W1b; t.W2 = p->W2b; t.W3 = p->W3b;
@@ -568,6 +569,8 @@ smap_status launch_forward(smap_proposal* p, const float* feat, const int* idx, 
         t.u = u;
         t.xout = xout;
         t.err = err ? err : p->tcerr;
+        t.wait_ns = wait_ns;
+        t.stall = stall;
         PCUDA(p, mlp_forward_tc_launch(t, num_sms(), st));
         g_launches.fetch_add(1);
         return SMAP_OK;
@@ -812,18 +815,29 @@ smap_status smap_proposal_fit_normalization(smap_proposal* p, const float* feat,
     return smap_proposal_set_weights(p, nullptr, norm.data());
 }
 
-smap_status smap_proposal_forward(smap_proposal* p, const float* feat, long rows, float* disp) {
+static smap_status forward_checked(smap_proposal* p, const float* feat, long rows, float* disp, uint64_t wait_ns,
+                                   int stall) {
     if (!p || !feat || !disp || rows < 1) return SMAP_E_INVAL;
-    smap_status s = launch_forward(p, feat, nullptr, rows, false, nullptr, disp, p->stream);
+    smap_status s = launch_forward(p, feat, nullptr, rows, false, nullptr, disp, p->stream, nullptr, wait_ns, stall);
     if (s) return s;
     int err = 0;
     PCUDA(p, cudaMemcpyAsync(&err, p->tcerr, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     PCUDA(p, cudaStreamSynchronize(p->stream));
     if (err) {
-        cudaMemsetAsync(p->tcerr, 0, sizeof(int), p->stream);
-        return pfail(p, SMAP_E_CUDA, "tensor-core forward: a wait gave up (results not written)");
+        PCUDA(p, cudaMemsetAsync(p->tcerr, 0, sizeof(int), p->stream));
+        PCUDA(p, cudaStreamSynchronize(p->stream));
+        return pfail(p, SMAP_E_TIMEOUT, "tensor-core forward: a bounded wait ran out (results not written)");
     }
     return SMAP_OK;
+}
+
+smap_status smap_proposal_forward(smap_proposal* p, const float* feat, long rows, float* disp) {
+    return forward_checked(p, feat, rows, disp, kTcWaitNs, 0);
+}
+
+smap_status smap_debug_proposal_forward(smap_proposal* p, const float* feat, long rows, float* disp,
+                                        uint64_t wait_ns, int stall) {
+    return forward_checked(p, feat, rows, disp, wait_ns, stall);
 }
 
 smap_status smap_proposal_loss_grad(smap_proposal* p, const float* feat, const float* targ, long rows, float* grad,

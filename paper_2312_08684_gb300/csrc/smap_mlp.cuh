@@ -42,7 +42,10 @@ struct MlpTcArgs {
     const float* u;                      // [rows][d] or null
     float* xout;                         // [rows][d]
     int* err;                            // set to 1 when a wait gave up (may be null)
+    uint64_t wait_ns;                    // limit of every bounded wait (global-timer nanoseconds)
+    int stall;                           // test only: the MMA lane first waits on a barrier nothing completes
 };
+constexpr uint64_t kTcWaitNs = 2000000000ull;   // default wait limit: 2 s
 size_t mlp_forward_tc_smem();
 cudaError_t mlp_forward_tc_launch(const MlpTcArgs& a, int num_sms, cudaStream_t st);
 

@@ -19,8 +19,9 @@
 // 16 j .. 16 j + 15 of every panel), so the MMA warp runs the next layer's K
 // steps while the GELU epilogue writes the following quarters. The next
 // tile's X goes into shared memory as soon as layer 3 completed, so its layer
-// 1 overlaps this tile's output epilogue. Every wait is bounded (about
-// 2 s); a wait that gives up sets *err and the CTA leaves its loop, frees its
+// 1 overlaps this tile's output epilogue. Every wait is bounded (a.wait_ns,
+// 2 s by default); a wait that gives up sets *err and the CTA leaves its loop,
+// waits (bounded) for the MMAs it already issued to complete, frees its
 // tensor memory and returns.
 //
 // Shared memory (offsets from a 1024-byte aligned base):
@@ -53,7 +54,7 @@ constexpr uint32_t kOffB3 = kOffB2 + 4 * kMlpH;
 constexpr uint32_t kOffNorm = kOffB3 + 4 * kMlpOutP;
 constexpr uint32_t kOffInvSd = kOffNorm + 4 * (2 * kMlpInP + 2 * kMlpOutP);   // 1 / sd_in
 constexpr uint32_t kOffBar = kOffInvSd + 4 * kMlpInP;
-constexpr int kNumBars = 10;
+constexpr int kNumBars = 12;
 constexpr uint32_t kOffTmem = kOffBar + 8 * kNumBars;
 constexpr uint32_t kTcSmemUsed = kOffTmem + 16;
 constexpr uint32_t kTcSmem = kTcSmemUsed + 1024;   // slack for aligning the base
@@ -66,7 +67,6 @@ constexpr uint32_t kOffX = kOffH + 2 * kPanelH;
 constexpr uint32_t kPanelW2 = kMlpH * 128;
 constexpr uint32_t kPanelW3 = kMlpOutP * 128;
 constexpr uint32_t kTmemCols = 512;
-constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr uint32_t kIdescN128 = tc::idesc_bf16_f32(128, 128);
 constexpr uint32_t kIdescN16 = tc::idesc_bf16_f32(128, 16);
 
@@ -198,6 +198,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_forward_tc_kernel(const __g
     uint64_t* bar_l3 = bar_l1 + 4;
     uint64_t* bar_x = bar_l1 + 5;
     uint64_t* bar_hq = bar_l1 + 6;   // [quarter]
+    // completion of every MMA issued (waited on only when giving up), and a
+    // barrier no thread ever completes (the stall test's wait)
+    uint64_t* bar_drain = bar_l1 + 10;
+    uint64_t* bar_never = bar_l1 + 11;
+    const uint64_t kWaitNs = a.wait_ns;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kOffTmem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -229,6 +234,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_forward_tc_kernel(const __g
         // one arrival per epilogue warp (after __syncwarp over its lanes' writes)
         tc::mbar_init(bar_x, kEpiWarps);
         for (int k = 0; k < 4; ++k) tc::mbar_init(bar_hq + k, kEpiWarps);
+        tc::mbar_init(bar_drain, 1);
+        tc::mbar_init(bar_never, 1);
         tc::mbar_init_fence();
     }
     if (warp == kEpiWarps) {
@@ -347,7 +354,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_forward_tc_kernel(const __g
         // Descriptors are built once; every MMA adds a compile-time byte offset
         // to the start-address field (all loops below are fully unrolled):
         // building them inside the issue loop costs far more than the MMA.
-        if (lane == 0) {
+        bool issued = false;
+        if (lane == 0 && a.stall && !tc::mbar_wait(bar_never, 0, kWaitNs)) ok = false;
+        if (lane == 0 && ok) {
             const uint64_t gX = tc::smem_desc(sb + kOffX, 512, tc::kSwizzle64);
             const uint64_t gW1 = tc::smem_desc(sb + kOffW1, 512, tc::kSwizzle64);
             const uint64_t gH = tc::smem_desc(sb + kOffH, 1024, tc::kSwizzle128);
@@ -356,6 +365,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_forward_tc_kernel(const __g
             for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
                 if (!tc::mbar_wait(bar_x, it & 1, kWaitNs)) { ok = false; break; }
                 tc::fence_after_sync();
+                issued = true;
                 // two 128-column halves, each committed on its own so that
                 // the epilogue warps of the first half start early
 #pragma unroll
@@ -405,7 +415,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_forward_tc_kernel(const __g
                 }
                 if (!ok) break;
             }
+            if (!ok && issued) {
+                // gave up with MMAs possibly in flight: they must complete
+                // before the tensor memory they write is freed
+                tc::mma_commit(bar_drain);
+                tc::mbar_wait(bar_drain, 0, kWaitNs);
+            }
         }
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
         __syncwarp();
     }
     if (!ok && lane == 0 && a.err) atomicExch(a.err, 1);

@@ -24,7 +24,7 @@ def _worker(rank, world, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
     ids = bench.shard(rank, world, 5)
-    wl = bench.make_workload(rank, 5, 3, 16, 2)
+    wl = bench.make_workload("C2", rank, 5)
     t = bench.max_over_ranks(10.0 + rank, dist)
     q.put((rank, ids, wl.x0.tolist(), t))
     dist.barrier()

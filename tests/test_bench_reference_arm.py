@@ -22,4 +22,4 @@ def test_reference_arm_json_line():
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
-    assert d["config"]["N"] == 256 and d["config"]["B"] == 1024
+    assert d["config"]["N"] == 512 and d["config"]["B"] == 4096 and d["config"]["L"] == 30

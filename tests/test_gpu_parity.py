@@ -395,3 +395,38 @@ def test_lane_split_variants_full_run(oracle, name):
             assert rel_err(hist[b, :T], ref["hist"]) <= 1e-3, (v, b)
             assert rel_err(path[b, : T + 1], ref["path"]) <= 1e-3, (v, b)
             assert J[b] == pytest.approx(ref["J"], rel=1e-3), (v, b)
+
+
+def test_autotune_times_every_variant_and_keeps_the_fastest(oracle):
+    """smap_autotune times every compiled launch shape that can hold N on a
+    sample of the batch, keeps the fastest, and leaves the handle at t = 0;
+    the run with the chosen shape still matches the oracle."""
+    wl = W.make_range_cv(B=6, T=10, N=64, L=5, dropout=(3, 6))
+    with Estimator.from_workload(wl) as est:
+        chosen, ms = est.autotune(wl.y, sample=2 * 152, steps=3)
+        nv = abi.smap_num_variants()
+        assert len(ms) == nv and 0 <= chosen < nv
+        assert np.all(np.isfinite(ms)) and np.all(ms > 0)     # every variant holds N = 64
+        assert ms[chosen] == np.min(ms)
+        assert est.variant()[0] == chosen
+        steps = np.empty(wl.B, np.int32)
+        abi.smap_get_steps(est.h, steps)
+        assert np.all(steps == 0)
+        path, J = est.run_batch(wl.y)
+    for b in range(wl.B):
+        ref = _run_oracle(oracle, wl, b)
+        assert rel_err(path[b], ref["path"]) <= 1e-3
+        assert J[b] == pytest.approx(ref["J"], rel=1e-3)
+
+
+def test_autotune_skips_variants_that_cannot_hold_N():
+    """At N = 512 the lane-split shapes (8 or 4 lanes per particle) exceed the
+    block size: they get no time and are never chosen."""
+    wl = W.make_clutter_cv(B=4, Tmin=3, Tmax=3, N=512, L=2)
+    with Estimator.from_workload(wl) as est:
+        chosen, ms = est.autotune(wl.y, sample=4, steps=2)
+    for v in range(abi.smap_num_variants()):
+        ppt, maxt, tpp = abi.smap_variant_info(v)
+        fits = ((512 + ppt - 1) // ppt) * tpp <= maxt
+        assert np.isfinite(ms[v]) == fits, v
+    assert np.isfinite(ms[chosen])

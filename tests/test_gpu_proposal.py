@@ -241,3 +241,147 @@ def test_learned_proposal_gains_over_plain_at_equal_iterations(torch, which):
         assert jl > j5
     finally:
         abi.smap_proposal_destroy(p)
+
+
+def test_forward_wait_that_runs_out_returns_timeout(torch):
+    """Every wait of the tensor-core forward is bounded. With stall = 1 the
+    MMA-issuing thread first waits on a barrier that nothing completes, so its
+    wait runs out before any MMA is issued, then the other warps' waits run
+    out: the call reports SMAP_E_TIMEOUT, and the next forward with the
+    default limit succeeds and matches a plain forward."""
+    p, n_in, n_out = _prop(torch, 3, W.clutter_params(), seed=6)
+    try:
+        rng = np.random.default_rng(8)
+        R = 152 * 128 + 5
+        feat = torch.zeros((R, INP), dtype=torch.float32, device="cuda")
+        feat[:, :n_in] = torch.from_numpy(rng.normal(0, 1, (R, n_in)).astype(np.float32)).cuda()
+        ref = torch.empty((R, n_out), dtype=torch.float32, device="cuda")
+        abi.smap_proposal_forward(p, feat, ref)
+        disp = torch.full((R, n_out), float("nan"), dtype=torch.float32, device="cuda")
+        for wait_ns in (0, 1_000_000):
+            with pytest.raises(abi.SmapError) as e:
+                abi.smap_debug_proposal_forward(p, feat, disp, wait_ns, stall=1)
+            assert e.value.status == abi.SMAP_E_TIMEOUT
+        abi.smap_debug_proposal_forward(p, feat, disp, 2_000_000_000, stall=0)
+        assert torch.equal(disp, ref)
+        disp.fill_(float("nan"))
+        abi.smap_proposal_forward(p, feat, disp)
+        assert torch.equal(disp, ref)
+    finally:
+        abi.smap_proposal_destroy(p)
+
+
+def test_adam_steps_match_oracle(oracle, torch):
+    """Two training steps on a one-row set (every minibatch row is that row)
+    against the oracle's Adam on the gradients the library reports at the same
+    weights: the FP32 master weights agree elementwise to FP32 rounding."""
+    p, n_in, n_out = _prop(torch, 4, W.arm_params(), seed=12)
+    try:
+        rng = np.random.default_rng(4)
+        feat = np.zeros((1, INP), np.float32); feat[0, :n_in] = rng.normal(0, 1, n_in)
+        targ = np.zeros((1, OUTP), np.float32); targ[0, :n_out] = rng.normal(0, 1, n_out)
+        fd, td = torch.from_numpy(feat).cuda(), torch.from_numpy(targ).cuda()
+        th0, _ = abi.smap_proposal_get_weights(p)
+        lr = 1e-3
+        theta = th0.astype(np.float64)
+        m = np.zeros_like(theta)
+        v = np.zeros_like(theta)
+        for step in (1, 2):
+            _, g = abi.smap_proposal_loss_grad(p, fd, td)      # gradient at the current weights
+            abi.smap_proposal_train(p, fd, td, 1, 1, lr, lr)
+            got, _ = abi.smap_proposal_get_weights(p)
+            oracle.adam(theta, g.astype(np.float64), m, v, step, lr)
+            tol = 2.0 ** -22 * np.abs(theta) + 1e-5 * lr
+            bad = np.abs(got - theta) > tol
+            assert not np.any(bad), (step, np.flatnonzero(bad)[:8])
+            assert np.any(got != th0)
+            theta = got.astype(np.float64)     # continue from the library's rounding
+    finally:
+        abi.smap_proposal_destroy(p)
+
+
+def _trained_prop(torch, mk_train, seed=9, steps=300):
+    """A proposal trained briefly on rows captured from a plain run (so that
+    its outputs lie inside the clamp, as a used network's do)."""
+    wl = mk_train()
+    p, n_in, n_out = _prop(torch, wl.kind, wl.params, seed=seed)
+    rows = int(np.sum(wl.T)) * wl.N
+    feat = torch.empty((rows, INP), dtype=torch.float32, device="cuda")
+    targ = torch.empty((rows, OUTP), dtype=torch.float32, device="cuda")
+    with Estimator.from_workload(wl) as est:
+        est.run_batch(wl.y, wl.T)
+        n = abi.smap_proposal_capture(p, est.h, feat, targ)
+    abi.smap_proposal_fit_normalization(p, feat[:n], targ[:n])
+    abi.smap_proposal_train(p, feat[:n], targ[:n], steps, 1024, 1e-3, 1e-4)
+    return p, n_in, n_out
+
+
+@pytest.mark.parametrize("which", ["clutter", "arm"])
+def test_learned_batched_run_matches_oracle_step_by_step(oracle, torch, which):
+    """The learned batched path (rows kernel -> tensor-core network -> one-step
+    SVGD kernel, two chains, graph-captured) held to the oracle at every step
+    of every sequence, each stage from the GPU's own inputs:
+      (i)   x^(0) - u against the oracle's perceptron on the BF16-rounded
+            weights, with u and the features recomputed by the oracle from the
+            GPU's previous set (within 3e-2 of the displacement spread);
+      (ii)  the step's final set against L_learned oracle SVGD iterations from
+            the GPU's x^(0) and previous set (1e-3 relative);
+      (iii) backpointers, path and J against the oracle's recursion on the
+            GPU's sets (identical where the margin exceeds 1e-6, J to 1e-12)."""
+    L = 5
+    if which == "clutter":
+        mk_train = lambda: W.make_clutter_cv(B=8, Tmin=6, Tmax=6, N=48, L=30, first=500)
+        wl = W.make_clutter_cv(B=3, Tmin=6, Tmax=6, N=48, L=L)
+    else:
+        mk_train = lambda: W.make_planar_arm(B=8, T=6, N=48, L=30, first=500)
+        wl = W.make_planar_arm(B=3, T=6, N=48, L=L)
+    p, n_in, n_out = _trained_prop(torch, mk_train)
+    try:
+        theta, norm = abi.smap_proposal_get_weights(p)
+        B, T, N, d = wl.B, wl.maxT, wl.N, wl.d
+        xinit = torch.full((B, T, N, d), float("nan"), dtype=torch.float32, device="cuda")
+        with Estimator.from_workload(wl) as est:
+            abi.smap_set_proposal(est.h, p, L)
+            abi.smap_debug_record_learned_init(est.h, xinit)
+            path, J = est.run_batch(wl.y, wl.T)
+            abi.smap_debug_record_learned_init(est.h, None)
+            hist = est.history()
+            psi = est.backpointers()
+        xi = xinit.cpu().numpy()
+        assert np.all(np.isfinite(xi))
+        m = oracle.Model(wl.kind, wl.params)
+        Wp = unpack(theta, n_in, n_out)
+        mu_in, sd_in = norm[:n_in], norm[INP:INP + n_in]
+        mu_out, sd_out = norm[2 * INP:2 * INP + n_out], norm[2 * INP + OUTP:2 * INP + OUTP + n_out]
+        got_disp, ref_disp, worst_svgd = [], [], 0.0
+        for b in range(B):
+            for t in range(1, T + 1):
+                z = wl.y[b, t - 1].astype(np.float64)
+                prev = wl.x0[b][None, :] if t == 1 else hist[b, t - 2].astype(np.float64)
+                fprev = np.array([m.transition(t, v) for v in prev])
+                a = fprev[np.zeros(N, int)] if t == 1 else fprev
+                u = np.array([a[i] + np.sqrt(m.q) * oracle.normals(wl.seed, b, t, i, d) for i in range(N)])
+                f = np.array([oracle.proposal_features(wl.kind, wl.params, u[i], z) for i in range(N)])
+                xn = bf16(((f - mu_in) / sd_in).astype(np.float32))
+                o = oracle.mlp_forward(n_in, H, n_out, Wp, xn)
+                ref_disp.append(np.clip(o, -8.0, 8.0) * sd_out + mu_out)
+                got_disp.append(xi[b, t - 1].astype(np.float64) - u)
+                # (ii) the SVGD iterations of the step from the GPU's x^(0)
+                xo, _ = m.svgd_iters(wl.prior, wl.bw_rule, wl.bw_value, t, z, fprev,
+                                     xi[b, t - 1].astype(np.float64), L, wl.step)
+                e = float(np.max(np.abs(hist[b, t - 1] - xo)) / max(1.0, np.sqrt(np.mean(xo * xo))))
+                worst_svgd = max(worst_svgd, e)
+        got_disp, ref_disp = np.concatenate(got_disp), np.concatenate(ref_disp)
+        spread = np.std(ref_disp, axis=0).max()
+        assert np.max(np.abs(got_disp - ref_disp)) <= 3e-2 * spread
+        assert worst_svgd <= 1e-3, worst_svgd
+        # (iii) the recursion on the GPU's own sets
+        for b in range(B):
+            h64, z64 = hist[b].astype(np.float64), wl.y[b].astype(np.float64)
+            ref = oracle.viterbi_sets(wl.kind, wl.params, wl.x0[b], h64, z64)
+            ok = oracle.viterbi_margins(wl.kind, wl.params, wl.x0[b], h64, z64) > 1e-6
+            assert np.array_equal(psi[b][ok], ref["psi"][ok])
+            assert J[b] == pytest.approx(ref["J"], rel=1e-12, abs=1e-9)
+            assert np.array_equal(path[b], ref["path"].astype(np.float32))
+    finally:
+        abi.smap_proposal_destroy(p)
