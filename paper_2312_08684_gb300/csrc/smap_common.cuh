@@ -183,6 +183,24 @@ __device__ inline double block_max_d(double v, double* red) {
 }
 
 // red: >= 33 floats of shared scratch.
+__device__ inline float block_max_f(float v, float* red) {
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane_id() == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        float s = (int)lane_id() < nw ? red[lane_id()] : -INFINITY;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s = fmaxf(s, __shfl_xor_sync(0xffffffffu, s, o));
+        if (lane_id() == 0) red[32] = s;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// red: >= 33 floats of shared scratch.
 __device__ inline float block_sum_f(float v, float* red) {
     const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     v = warp_sum_f(v);

@@ -1047,48 +1047,67 @@ __device__ __forceinline__ double trans_m64(const ModelParams& mp, const float* 
 
 // ---------------------------------------------------------------------------
 // a7: forward recursion. The argmax over j of phi_{t-1}(j) + log p(x_i | x^j)
-// is screened in FP32 with a rigorous rounding bound (centred coordinates
-// scaled by Q^-1/2 kKm, where m~ = kKm^2 |x_i - f_j|^2_{Q^-1}), and every j
-// that can still be the FP64 maximum is evaluated in FP64; phi_t is
-// accumulated in FP64. Lowest j wins ties.
-// On return: best[p], phinew[p] for the block's particles.
+// is screened in FP32 with a rigorous rounding bound, and every j that can
+// still be the FP64 maximum is evaluated in FP64; phi_t is accumulated in
+// FP64. Lowest j wins ties.
+//
+// Screen (dot-product form). With X_i = (x_i - c) Q^-1/2 and Y_j = (f_j - c)
+// Q^-1/2 the score is, up to a term of i alone,
+//   S_ij = A_j + X_i . Y_j,   A_j = phi_{t-1}(j) - max_k phi_{t-1}(k) - |Y_j|^2 / 2,
+// so one pair costs d FMAs of x~ = kKm X against g = kLam f~ = Y / kKm (x~ . g
+// = X . Y, as kKm^2 kLam = 1) plus the running top two. Rounding (u = 2^-24,
+// first order): x~ carries 4u relative error per coordinate, g 3u, and the
+// FP32 constants kKm^2 kLam differ from 1 by 1.5u, so x~ . g is within
+// 7.5u |X_i| |Y_j| of X . Y; A_j in FP32 from the FP32 phi~ and f~ is within
+// (d + 6.5) u H_j of the exact value, H_j = |phi~_j| + kLam |f~_j|^2 / 2; the
+// start value aU_j = A_j + e_j adds u (H_j + e_j); the FMA chain adds
+// d u (|aU_j| + |x~_i| |g_j|). With e_j = (2d + 8) u H_j (1.01) plus a margin
+// for the FP64 evaluation's own rounding, and E_i = (d + 8) u |x~_i| max_j |g_j|
+// (1.01) (plus the same margin), the computed chain v_ij satisfies
+//   v_ij - 2 e_j - E_i <= S_ij <= v_ij + E_i.
+// So with v1 = max_j v_ij at j1 (first j attaining it) and v2 the largest v_ij
+// of every other j, v1 - v2 > 2 e_j1 + 2 E_i proves j1 the unique maximum of
+// S (and of its FP64 evaluation). Otherwise (a near-tie) every j with
+// v_ij >= v1 - 2 e_j1 - 2 E_i is evaluated in FP64, lowest j first.
+// On return: best[p], phinew[p] for the block's particles. fs is overwritten
+// (g_j replaces f~_j).
 // ---------------------------------------------------------------------------
 template <class M, int PPT>
 __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, const double* f64,
                              int* best, double* phinew) {
     constexpr int D = M::D, DP = M::DP;
     const int tid = threadIdx.x, NT = blockDim.x;
-    // Rounding allowance of the FP32 scores, u = 2^-24. With the exact scaled
-    // difference e* and the error D of the computed one (|D| <= 5u|x~| + u|f~|
-    // per coordinate: the FP32 centring, the FP32 scale, the FP32 copy of the
-    // FP64 mean), 2|e*||D| <= g u e*^2 + D^2 / (g u) for any g > 0; with
-    // g = 50 the computed distance m~ is within u (67 m~ + (|x~|^2 + |f~|^2))
-    // of the exact one (first order, d <= 14, the subtraction and the FMA
-    // chain included). In score units (kLam / 2 per unit of m~) the allowance
-    // below is u (128 m~ + 4 (|x~|^2 + |f~|^2)) kLam / 2, and 8u |phi~| for
-    // the FP32 copy of phi_{t-1}(j) - max and the two roundings of L and U (3u):
-    // at least 1.8x each bound.
-    const float Ku = 3.814697265625e-06f;    // 64 u: per unit of kLam m~
-    const float Kf = 1.1920928955078125e-07f; // 2 u: per unit of kLam (|x~|^2 + |f~|^2)
-    const float Kp = 4.76837158203125e-07f;   // 8 u: per unit of |phi~|
+    constexpr float u = 5.9604644775390625e-08f;   // 2^-24
+    constexpr float Ke = (2 * D + 8) * u * 1.01f;   // e_j per unit of H_j
+    constexpr float Ki = (D + 8) * u * 1.01f;       // E_i per unit of |x~_i| max |g|
+    constexpr double K64 = 1.4210854715202004e-14;  // 2^-46: margin of the FP64 scores
     double pmax = -INFINITY;
     for (int j = tid; j < Np; j += NT) pmax = fmax(pmax, s.phis[j]);
     pmax = block_max_d(pmax, s.redd);
-    float2* ab = reinterpret_cast<float2*>(s.gs);
+    float2* ab = reinterpret_cast<float2*>(s.gs);   // (aU_j, 2 e_j)
+    float gmax2 = 0.0f;
     for (int j = tid; j < Np; j += NT) {
         const double dphi = s.phis[j] - pmax;
         const float ph = (float)dphi;
         float fr[D];
         load_row<D, DP>(s.fs, j, fr);
-        float F = 0.0f;
+        float F = 0.0f, G = 0.0f;
 #pragma unroll
-        for (int c = 0; c < D; ++c) F = fmaf(fr[c], fr[c], F);
-        const float B = Kf * kLam * F + Kp * fabsf(ph) +
-                        (float)(4.4408920985006262e-16 * (fabs(s.phis[j]) + fabs(pmax)));
-        ab[j] = make_float2(ph + B, ph - B);
+        for (int c = 0; c < D; ++c) {
+            F = fmaf(fr[c], fr[c], F);
+            fr[c] *= kLam;
+            G = fmaf(fr[c], fr[c], G);
+        }
+        store_row<D, DP>(s.fs, j, fr);
+        gmax2 = fmaxf(gmax2, G);
+        const float half = 0.5f * kLam * F;
+        const float H = fabsf(ph) + half;
+        const float e = Ke * H + (float)(K64 * (fabs(s.phis[j]) + fabs(pmax) + fabs(mp.logtrans_c) +
+                                                (double)(kLam * F)));
+        ab[j] = make_float2((ph - half) + e, 2.0f * e);
     }
-    __syncthreads();
-    float xc[PPT][D], C[PPT], Lmax[PPT];
+    const float gmax = sqrtf(block_max_f(gmax2, s.redf)) * 1.0000005f;
+    float xc[PPT][D], Ei[PPT];
     float cf[D], qk[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) {
@@ -1106,38 +1125,42 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
             xc[p][c] = (xr[c] - cf[c]) * qk[c];
             X = fmaf(xc[p][c], xc[p][c], X);
         }
-        C[p] = Kf * kLam * X;
-        Lmax[p] = -INFINITY;
+        Ei[p] = Ki * sqrtf(X) * 1.0000005f * gmax + (float)(K64 * (double)(kLam * X));
     }
-    const float cl = -(0.5f + Ku) * kLam, cu = -(0.5f - Ku) * kLam;
-    // One FP32 pass: per particle the best lower bound L1 (first j attaining
-    // it), that j's upper bound U1, and the largest upper bound Uo of every
-    // other j. Uo < L1 proves j1 the unique FP64 maximum, so each lane then
-    // evaluates one FP64 score, all lanes together (no divergent FP64 work).
-    float L1[PPT], U1[PPT], Uo[PPT];
+    // One FP32 pass: per particle the largest chain value v1 (first j
+    // attaining it) and the largest value v2 of every other j.
+    float v1[PPT], v2[PPT];
     int j1[PPT];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
-        L1[p] = -INFINITY;
-        U1[p] = -INFINITY;
-        Uo[p] = -INFINITY;
+        v1[p] = -INFINITY;
+        v2[p] = -INFINITY;
         j1[p] = 0;
     }
     for (int j = 0; j < Np; ++j) {
-        float fj[D];
-        load_row<D, DP>(s.fs, j, fj);
-        const float2 abj = ab[j];
+        float gj[D];
+        load_row<D, DP>(s.fs, j, gj);
+        const float aU = ab[j].x;
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
-            const float dist = sqdist<D>(xc[p], fj);
-            const float L = fmaf(cl, dist, abj.y - C[p]);
-            const float U = fmaf(cu, dist, abj.x + C[p]);
-            const bool nb = L > L1[p];
-            Uo[p] = fmaxf(Uo[p], nb ? U1[p] : U);
-            U1[p] = nb ? U : U1[p];
-            L1[p] = nb ? L : L1[p];
+            float v = aU;
+#pragma unroll
+            for (int c = 0; c < D; ++c) v = fmaf(xc[p][c], gj[c], v);
+            const bool nb = v > v1[p];
             j1[p] = nb ? j : j1[p];
+            const float lo = fminf(v1[p], v);
+            v1[p] = fmaxf(v1[p], v);
+            v2[p] = fmaxf(v2[p], lo);
         }
+    }
+    // candidate threshold: v_ij >= v1 - 2 e_j1 - 2 E_i can still be the maximum
+    float thr[PPT];
+    bool uniq[PPT];
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        const float m = (ab[j1[p]].y + 2.0f * Ei[p]) * 1.0000005f;
+        uniq[p] = (v1[p] - v2[p]) > m;
+        thr[p] = v1[p] - m;
     }
     double bs[PPT], blt[PPT];
     int row[PPT];
@@ -1148,7 +1171,7 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
         bs[p] = -INFINITY;
         blt[p] = 0.0;
         best[p] = 0;
-        if (Uo[p] < L1[p]) {
+        if (uniq[p]) {
             const int j = j1[p];
             blt[p] = mp.logtrans_c - 0.5 * trans_m64<D>(mp, s.xs + row[p], f64 + (size_t)j * D);
             bs[p] = s.phis[j] + blt[p];
@@ -1158,17 +1181,18 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
         }
     }
     if (multi) {
-        // near-ties (rare): every j whose upper bound reaches L1, in FP64,
-        // lowest j first
+        // near-ties (rare): every candidate j in FP64, lowest j first
         for (int j = 0; j < Np; ++j) {
-            float fj[D];
-            load_row<D, DP>(s.fs, j, fj);
-            const float ap = ab[j].x;
+            float gj[D];
+            load_row<D, DP>(s.fs, j, gj);
+            const float aU = ab[j].x;
 #pragma unroll
             for (int p = 0; p < PPT; ++p) {
-                if (Uo[p] < L1[p]) continue;
-                const float U = fmaf(cu, sqdist<D>(xc[p], fj), ap + C[p]);
-                if (U >= L1[p]) {
+                if (uniq[p]) continue;
+                float v = aU;
+#pragma unroll
+                for (int c = 0; c < D; ++c) v = fmaf(xc[p][c], gj[c], v);
+                if (v >= thr[p]) {
                     const double lt = mp.logtrans_c - 0.5 * trans_m64<D>(mp, s.xs + row[p], f64 + (size_t)j * D);
                     const double sv = s.phis[j] + lt;
                     if (sv > bs[p]) { bs[p] = sv; blt[p] = lt; best[p] = j; }

@@ -244,18 +244,37 @@ struct ModelClutterCV : CVTransition {
         const float k = rinv / s;
         g[0] = a0 * k; g[1] = a1 * k; g[2] = 0.0f; g[3] = 0.0f;
     }
+    // log of the mixture by a max-shifted sum. A term more than 40 nats below
+    // the largest adds less than e^-40 < 2^-57 to a sum that is at least 1,
+    // below the FP64 rounding of the result: such terms are found with an
+    // FP32 pass (its error is far inside the 5-nat margin) and skipped, so
+    // that the FP64 work is the few terms near the maximum (usually the
+    // true point's and the outlier term).
     __device__ static double loglik64(const ModelParams& mp, const float* z, const double* x) {
         const int M = (int)mp.p[6];
         const double rinv = 1.0 / mp.p[5];
+        const float xf0 = (float)x[0], xf1 = (float)x[1];
+        const float c2 = -0.5f * mp.auxf[0];
+        const float a0f = (float)mp.aux[0], a1f = (float)mp.aux[1];
+        float mxf = a1f;
+        for (int m = 0; m < M; ++m) {
+            const float ex = z[2 * m] - xf0, ey = z[2 * m + 1] - xf1;
+            mxf = fmaxf(mxf, fmaf(c2, fmaf(ex, ex, ey * ey), a0f));
+        }
+        const float keep = mxf - 45.0f;
         double mx = mp.aux[1];
         for (int m = 0; m < M; ++m) {
-            const double ex = (double)z[2 * m] - x[0], ey = (double)z[2 * m + 1] - x[1];
-            mx = fmax(mx, mp.aux[0] - 0.5 * (ex * ex + ey * ey) * rinv);
+            const float ex = z[2 * m] - xf0, ey = z[2 * m + 1] - xf1;
+            if (fmaf(c2, fmaf(ex, ex, ey * ey), a0f) < keep) continue;
+            const double ed = (double)z[2 * m] - x[0], fd = (double)z[2 * m + 1] - x[1];
+            mx = fmax(mx, mp.aux[0] - 0.5 * (ed * ed + fd * fd) * rinv);
         }
-        double s = exp(mp.aux[1] - mx);
+        double s = (a1f < keep) ? 0.0 : exp(mp.aux[1] - mx);
         for (int m = 0; m < M; ++m) {
-            const double ex = (double)z[2 * m] - x[0], ey = (double)z[2 * m + 1] - x[1];
-            s += exp(mp.aux[0] - 0.5 * (ex * ex + ey * ey) * rinv - mx);
+            const float ex = z[2 * m] - xf0, ey = z[2 * m + 1] - xf1;
+            if (fmaf(c2, fmaf(ex, ex, ey * ey), a0f) < keep) continue;
+            const double ed = (double)z[2 * m] - x[0], fd = (double)z[2 * m + 1] - x[1];
+            s += exp(mp.aux[0] - 0.5 * (ed * ed + fd * fd) * rinv - mx);
         }
         return mx + log(s);
     }

@@ -72,15 +72,23 @@ def test_duplicated_particles_take_the_radix_select(oracle):
     assert c[2] == 2 * wl.B and c[0] == 0
 
 
-def test_far_cluster_defeats_the_guess(oracle):
-    """The 32 particles that the first median guess pairs with others sit
-    10^4 away from the rest: the guess (a mean of those pair distances) is
-    more than 4 octaves above the median (a distance inside the near
-    cluster), the histogram around it cannot locate the middle ranks, and the
-    radix select takes over; the next iteration brackets the exact median."""
+def test_far_outliers_defeat_the_guess(oracle):
+    """The 32 particles that the first median guess pairs with others sit 100
+    units from the rest, each in its own direction (so every pair distance
+    that involves one of them is far above the median): the guess (a mean of
+    those pair distances) is more than 4 octaves above the median, the
+    histogram around it cannot locate the middle ranks, and the radix select
+    takes over; the next iteration brackets the exact median.
+
+    (Pair distances are formed as |x_i|^2 + |x_k|^2 - 2 x_i . x_k in FP32, so
+    a tight cluster far from the centre of the set gets distances with an
+    absolute error of a few u (|x_i|^2 + |x_k|^2); the outliers here are
+    spread out, which keeps every distance near the median exact enough.)"""
     wl, t, xprev, xinit = _range_sets(256, 3)
     far = (7 * np.arange(32)) % 256
-    xinit[:, far, :2] += 1e4
+    ang = 2.0 * np.pi * np.arange(32) / 32.0
+    xinit[:, far, 0] += (100.0 * np.cos(ang)).astype(np.float32)
+    xinit[:, far, 1] += (100.0 * np.sin(ang)).astype(np.float32)
     c = _run(oracle, wl, t, xprev, xinit, 2)
     assert c[2] == wl.B and c[0] == wl.B
 
