@@ -138,7 +138,11 @@ typedef struct {
 
 /* Validates cfg, allocates the handle's device buffers (particle history
  * [B][max_T][N][d] FP32, backpointers [B][max_T][N] uint16, scores [B][N]
- * FP64, work queue and scratch). No kernel runs. *out is NULL on failure. */
+ * FP64, work queue and scratch). No kernel runs. *out is NULL on failure;
+ * a failed allocation returns SMAP_E_NOMEM and frees what was allocated.
+ * (For tests, the environment variable SMAP_FAIL_ALLOC=k makes the k-th
+ * device allocation of a call fail that way.) The library marks the host
+ * phases of its entry points with NVTX ranges named after them. */
 smap_status smap_create(const smap_config* cfg, smap_handle** out);
 
 /* Frees everything the handle owns (synchronises its stream). NULL is a no-op. */
@@ -192,6 +196,23 @@ smap_status smap_get_steps(smap_handle* h, int* t_per_seq);
 smap_status smap_viterbi(smap_handle* h, const float* hist, const float* y_all,
                          const int* T_per_seq, const int* N_per_seq, float* path,
                          double* J, uint16_t* psi, int on_device);
+
+/* Checkpoint and resume of the online state (not in the paper): the known
+ * x_0, every sequence's step count, particle count, length and status, the
+ * current scores phi_t [B][N], the median guesses of the bandwidth rule, and
+ * each sequence's particle sets and backpointer rows up to its current step.
+ * smap_state_size gives the bytes smap_save writes now (it grows with the
+ * step counts). smap_save copies the state into host memory `buf` of at
+ * least that size (synchronises the stream; the handle is not changed).
+ * smap_load restores it into a handle created with the same configuration
+ * (model, parameters, N, L, step, bandwidth rule and value, prior, kernel,
+ * seed, batch, max_T): SMAP_E_INVAL if the configuration or the sizes do not
+ * match. After smap_load, smap_step continues exactly as the saved handle
+ * would have (same bits). An attached proposal is not part of the state
+ * (smap_proposal_get_weights / set_weights save and restore it). */
+smap_status smap_state_size(const smap_handle* h, size_t* bytes);
+smap_status smap_save(smap_handle* h, void* buf, size_t bytes);
+smap_status smap_load(smap_handle* h, const void* buf, size_t bytes);
 
 /* PF-MAP-Seq, the particle-filter comparison method of Section V (Godsill,
  * Doucet and West 2001): for every sequence a bootstrap particle filter with

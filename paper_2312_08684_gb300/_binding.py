@@ -35,6 +35,7 @@ EXPORTS = [
     "smap_proposal_set_weights", "smap_proposal_fit_normalization", "smap_proposal_forward",
     "smap_proposal_loss_grad", "smap_proposal_train", "smap_proposal_last_error", "smap_proposal_capture",
     "smap_set_proposal", "smap_pf_run_batch", "smap_debug_proposal_forward", "smap_debug_record_learned_init",
+    "smap_state_size", "smap_save", "smap_load",
 ]
 MLP_IN_P, MLP_OUT_P, MLP_H = 32, 16, 256
 
@@ -116,6 +117,9 @@ def load():
     L.smap_set_proposal.argtypes = [_VP, _VP, _I]
     L.smap_debug_proposal_forward.argtypes = [_VP, _VP, ctypes.c_long, _VP, ctypes.c_uint64, _I]
     L.smap_debug_record_learned_init.argtypes = [_VP, _VP]
+    L.smap_state_size.argtypes = [_VP, ctypes.POINTER(ctypes.c_size_t)]
+    L.smap_save.argtypes = [_VP, _VP, ctypes.c_size_t]
+    L.smap_load.argtypes = [_VP, _VP, ctypes.c_size_t]
     L.smap_viterbi_noalloc.argtypes = [_I, ctypes.POINTER(ctypes.c_double), _I, _I, _I, _I,
                                        _VP, _VP, _VP, _VP, _VP, _VP]
     L.smap_kernel_launches.argtypes = []
@@ -464,6 +468,24 @@ def smap_debug_record_learned_init(h, xinit_all=None):
     """xinit_all: CUDA tensor [B][max_T][N][d] float32, or None to stop recording."""
     ptr = None if xinit_all is None else _dev(xinit_all, np.float32)
     _check(load().smap_debug_record_learned_init(h, ptr), h)
+
+
+def smap_state_size(h):
+    n = ctypes.c_size_t()
+    _check(load().smap_state_size(h, ctypes.byref(n)), h)
+    return int(n.value)
+
+
+def smap_save(h):
+    """The handle's online state as a host byte array (see include/smap.h)."""
+    buf = np.empty(smap_state_size(h), np.uint8)
+    _check(load().smap_save(h, ctypes.c_void_p(buf.ctypes.data), buf.nbytes), h)
+    return buf
+
+
+def smap_load(h, buf):
+    buf = np.ascontiguousarray(buf, np.uint8)
+    _check(load().smap_load(h, ctypes.c_void_p(buf.ctypes.data), buf.nbytes), h)
 
 
 def smap_kernel_launches():

@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <numeric>
@@ -556,9 +557,143 @@ smap_status batch_device_work(smap_handle* h, int v) {
     return SMAP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Checkpoint of the online state: a header that identifies the handle's
+// configuration, then x0 [B][d] FP64, tcur / Nseq / Tend / status [B] int32,
+// the median guesses [B] FP32, the scores phi [B][N] FP64, and for every
+// sequence b its first tcur[b] particle sets [tcur_b][N][d] FP32 and
+// backpointer rows [tcur_b][N] uint16.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kStateMagic = 0x31765453'50414D53ull;   // "SMAPSTv1"
+
+struct StateHeader {
+    uint64_t magic, bytes, params_hash, seed;
+    int32_t model, d, dy, B, Nmax, maxT, L, bw_rule, prior, kernel, n_params, reserved;
+    double step, bw_value;
+};
+
+uint64_t params_hash(const std::vector<double>& p) {
+    uint64_t x = 1469598103934665603ull;   // FNV-1a over the bytes of the vector
+    const unsigned char* c = reinterpret_cast<const unsigned char*>(p.data());
+    for (size_t k = 0; k < p.size() * sizeof(double); ++k) x = (x ^ c[k]) * 1099511628211ull;
+    return x;
+}
+
+StateHeader state_header(const smap_handle* h) {
+    StateHeader H;
+    memset(&H, 0, sizeof(H));
+    H.magic = kStateMagic;
+    H.params_hash = params_hash(h->params);
+    H.seed = h->cfg.seed;
+    H.model = h->cfg.model; H.d = h->d; H.dy = h->dy; H.B = h->B; H.Nmax = h->Nmax; H.maxT = h->maxT;
+    H.L = h->cfg.L; H.bw_rule = h->cfg.bw_rule; H.prior = h->cfg.prior; H.kernel = h->cfg.kernel;
+    H.n_params = (int32_t)h->params.size();
+    H.step = h->cfg.step; H.bw_value = h->cfg.bw_value;
+    return H;
+}
+
+size_t state_bytes(const smap_handle* h, const std::vector<int>& tcur) {
+    size_t n = sizeof(StateHeader) + sizeof(double) * (size_t)h->B * h->d + sizeof(int32_t) * 4 * (size_t)h->B +
+               sizeof(float) * (size_t)h->B + sizeof(double) * (size_t)h->B * h->Nmax;
+    for (int b = 0; b < h->B; ++b)
+        n += (size_t)tcur[b] * h->Nmax * (sizeof(float) * h->d + sizeof(uint16_t));
+    return n;
+}
+
 }  // namespace
 
 extern "C" {
+
+smap_status smap_state_size(const smap_handle* h, size_t* bytes) {
+    if (!h || !bytes) return SMAP_E_INVAL;
+    *bytes = state_bytes(h, h->tcur_h);
+    return SMAP_OK;
+}
+
+smap_status smap_save(smap_handle* h, void* buf, size_t bytes) {
+    NvtxRange nvtx_("smap_save");
+    smap_status st = check_usable(h);
+    if (st) return st;
+    const size_t need = state_bytes(h, h->tcur_h);
+    if (!buf || bytes < need) return fail(h, SMAP_E_INVAL, "smap_save: buffer smaller than smap_state_size");
+    unsigned char* o = static_cast<unsigned char*>(buf);
+    StateHeader H = state_header(h);
+    H.bytes = need;
+    memcpy(o, &H, sizeof(H));
+    o += sizeof(H);
+    const size_t B = h->B, N = h->Nmax, d = h->d, T = h->maxT;
+    auto d2h = [&](const void* src, size_t n) -> cudaError_t {
+        const cudaError_t e = cudaMemcpyAsync(o, src, n, cudaMemcpyDeviceToHost, h->stream);
+        o += n;
+        return e;
+    };
+    SMAP_CUDA(h, d2h(h->x0, sizeof(double) * B * d));
+    SMAP_CUDA(h, d2h(h->tcur, sizeof(int) * B));
+    SMAP_CUDA(h, d2h(h->Nseq, sizeof(int) * B));
+    SMAP_CUDA(h, d2h(h->Tend, sizeof(int) * B));
+    SMAP_CUDA(h, d2h(h->status, sizeof(int) * B));
+    SMAP_CUDA(h, d2h(h->bwguess, sizeof(float) * B));
+    SMAP_CUDA(h, d2h(h->phi, sizeof(double) * B * N));
+    for (size_t b = 0; b < B; ++b)
+        if (h->tcur_h[b] > 0) SMAP_CUDA(h, d2h(h->hist + b * T * N * d, sizeof(float) * h->tcur_h[b] * N * d));
+    for (size_t b = 0; b < B; ++b)
+        if (h->tcur_h[b] > 0) SMAP_CUDA(h, d2h(h->psi + b * T * N, sizeof(uint16_t) * h->tcur_h[b] * N));
+    SMAP_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SMAP_OK;
+}
+
+smap_status smap_load(smap_handle* h, const void* buf, size_t bytes) {
+    NvtxRange nvtx_("smap_load");
+    smap_status st = check_usable(h);
+    if (st) return st;
+    if (!buf || bytes < sizeof(StateHeader)) return fail(h, SMAP_E_INVAL, "smap_load: no state");
+    StateHeader H;
+    memcpy(&H, buf, sizeof(H));
+    StateHeader mine = state_header(h);
+    mine.bytes = H.bytes;
+    if (memcmp(&H, &mine, sizeof(H)) != 0)
+        return fail(h, SMAP_E_INVAL, "smap_load: the state was saved by a handle of another configuration");
+    const size_t B = h->B, N = h->Nmax, d = h->d, T = h->maxT;
+    const unsigned char* in = static_cast<const unsigned char*>(buf) + sizeof(H);
+    const size_t fixed = sizeof(H) + sizeof(double) * B * d + sizeof(int32_t) * 4 * B + sizeof(float) * B +
+                         sizeof(double) * B * N;
+    if (bytes < fixed || H.bytes > bytes) return fail(h, SMAP_E_INVAL, "smap_load: truncated state");
+    std::vector<int> tc(B), ns(B), te(B);
+    memcpy(tc.data(), in + sizeof(double) * B * d, sizeof(int) * B);
+    memcpy(ns.data(), in + sizeof(double) * B * d + sizeof(int) * B, sizeof(int) * B);
+    memcpy(te.data(), in + sizeof(double) * B * d + 2 * sizeof(int) * B, sizeof(int) * B);
+    for (size_t b = 0; b < B; ++b)
+        if (tc[b] < 0 || tc[b] > (int)T || ns[b] < 1 || ns[b] > (int)N || te[b] < 1 || te[b] > (int)T)
+            return fail(h, SMAP_E_INVAL, "smap_load: step counts or particle counts out of range");
+    if (H.bytes != state_bytes(h, tc)) return fail(h, SMAP_E_INVAL, "smap_load: size does not match its contents");
+    std::vector<double> x0(B * d);
+    memcpy(x0.data(), in, sizeof(double) * B * d);
+    for (double v : x0)
+        if (!std::isfinite(v)) return fail(h, SMAP_E_NONFINITE, "smap_load: x0 not finite");
+    auto h2d = [&](void* dst, size_t n) -> cudaError_t {
+        const cudaError_t e = cudaMemcpyAsync(dst, in, n, cudaMemcpyHostToDevice, h->stream);
+        in += n;
+        return e;
+    };
+    SMAP_CUDA(h, h2d(h->x0, sizeof(double) * B * d));
+    SMAP_CUDA(h, h2d(h->tcur, sizeof(int) * B));
+    SMAP_CUDA(h, h2d(h->Nseq, sizeof(int) * B));
+    SMAP_CUDA(h, h2d(h->Tend, sizeof(int) * B));
+    SMAP_CUDA(h, h2d(h->status, sizeof(int) * B));
+    SMAP_CUDA(h, h2d(h->bwguess, sizeof(float) * B));
+    SMAP_CUDA(h, h2d(h->phi, sizeof(double) * B * N));
+    for (size_t b = 0; b < B; ++b)
+        if (tc[b] > 0) SMAP_CUDA(h, h2d(h->hist + b * T * N * d, sizeof(float) * tc[b] * N * d));
+    for (size_t b = 0; b < B; ++b)
+        if (tc[b] > 0) SMAP_CUDA(h, h2d(h->psi + b * T * N, sizeof(uint16_t) * tc[b] * N));
+    SMAP_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->x0h = x0;
+    h->cfg.x0 = h->x0h.data();
+    h->tcur_h = tc;
+    h->Nseq_h = ns;
+    h->Tend_h = te;
+    return SMAP_OK;
+}
 
 const char* smap_status_string(smap_status s) {
     switch (s) {
@@ -618,6 +753,7 @@ smap_status smap_debug_record_learned_init(smap_handle* h, float* xinit_all) {
 
 smap_status smap_proposal_capture(smap_proposal* p, smap_handle* h, float* feat, float* targ, long max_rows,
                                   long* rows) {
+    NvtxRange nvtx_("smap_proposal_capture");
     smap_status st = check_usable(h);
     if (st) return st;
     if (!p || !feat || !targ) return fail(h, SMAP_E_INVAL, "null argument");
@@ -703,6 +839,7 @@ void smap_destroy(smap_handle* h) {
 }
 
 smap_status smap_create(const smap_config* cfg, smap_handle** out) {
+    NvtxRange nvtx_("smap_create");
     if (!out) return SMAP_E_INVAL;
     *out = nullptr;
     if (!cfg) return SMAP_E_INVAL;
@@ -776,7 +913,14 @@ smap_status smap_create(const smap_config* cfg, smap_handle** out) {
         {(void**)&h->path, sizeof(float) * B * (T + 1) * d},
         {(void**)&h->J, sizeof(double) * B},
     };
+    // fault injection for tests: SMAP_FAIL_ALLOC=k makes the k-th device
+    // allocation of this call fail as if the device were out of memory
+    const char* inj = std::getenv("SMAP_FAIL_ALLOC");
+    const int fail_at = inj ? std::atoi(inj) : 0;
+    int n_alloc = 0;
     for (auto& al : allocs) {
+        if (++n_alloc == fail_at)
+            return bail(SMAP_E_NOMEM, "cudaMalloc: injected failure (SMAP_FAIL_ALLOC)");
         e = cudaMalloc(al.p, al.bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -859,6 +1003,7 @@ smap_status smap_get_variant(const smap_handle* h, int* v, int* threads, int* gr
 }
 
 smap_status smap_step(smap_handle* h, const float* y, const uint8_t* active, int on_device) {
+    NvtxRange nvtx_("smap_step");
     smap_status st = check_usable(h);
     if (st) return st;
     if (!y) return fail(h, SMAP_E_INVAL, "y is null");
@@ -891,6 +1036,7 @@ smap_status smap_step(smap_handle* h, const float* y, const uint8_t* active, int
 }
 
 smap_status smap_map_sequence(smap_handle* h, float* path, double* J, int on_device) {
+    NvtxRange nvtx_("smap_map_sequence");
     smap_status st = check_usable(h);
     if (st) return st;
     st = launch_backtrack(h);
@@ -902,6 +1048,7 @@ smap_status smap_map_sequence(smap_handle* h, float* path, double* J, int on_dev
 
 smap_status smap_run_batch(smap_handle* h, const float* y_all, const int* T_per_seq, const int* N_per_seq,
                            float* path, double* J, int on_device) {
+    NvtxRange nvtx_("smap_run_batch");
     smap_status st = check_usable(h);
     if (st) return st;
     if (!y_all) return fail(h, SMAP_E_INVAL, "y_all is null");
@@ -981,6 +1128,7 @@ smap_status smap_get_steps(smap_handle* h, int* t) {
 
 smap_status smap_viterbi(smap_handle* h, const float* hist, const float* y_all, const int* T_per_seq,
                          const int* N_per_seq, float* path, double* J, uint16_t* psi, int on_device) {
+    NvtxRange nvtx_("smap_viterbi");
     smap_status st = check_usable(h);
     if (st) return st;
     if (!hist || !y_all) return fail(h, SMAP_E_INVAL, "null input");
@@ -1008,6 +1156,7 @@ smap_status smap_viterbi(smap_handle* h, const float* hist, const float* y_all, 
 
 smap_status smap_pf_run_batch(smap_handle* h, const float* y_all, const int* T_per_seq, const int* N_per_seq,
                               float* path, double* J, int on_device) {
+    NvtxRange nvtx_("smap_pf_run_batch");
     smap_status st = check_usable(h);
     if (st) return st;
     if (!y_all) return fail(h, SMAP_E_INVAL, "y_all is null");
@@ -1072,6 +1221,7 @@ smap_status smap_pf_run_batch(smap_handle* h, const float* y_all, const int* T_p
 
 smap_status smap_autotune(smap_handle* h, const float* y_all, int sample, int steps, int on_device,
                           int* chosen, float* ms_per_variant, int n_ms) {
+    NvtxRange nvtx_("smap_autotune");
     smap_status st = check_usable(h);
     if (st) return st;
     if (!y_all || sample < 1 || steps < 1) return fail(h, SMAP_E_INVAL, "autotune: bad arguments");

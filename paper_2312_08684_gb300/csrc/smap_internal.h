@@ -4,6 +4,8 @@
 #include <atomic>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "smap.h"
 #include "smap_common.cuh"
 
@@ -64,6 +66,15 @@ smap_status proposal_launch_init(smap_proposal* p, const ProposalRowsArgs& ra, f
 smap_status proposal_launch_capture(smap_proposal* p, const ProposalRowsArgs& ra, cudaStream_t st);
 int proposal_kind(const smap_proposal* p);
 int proposal_d(const smap_proposal* p);
+
+// A named NVTX range over the lifetime of the object (a no-op unless a
+// profiler is attached): the entry points mark their host-side phases.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Shared by the ABI translation units (defined in smap_api.cu).
 extern std::atomic<uint64_t> g_launches;

@@ -817,6 +817,7 @@ smap_status smap_proposal_fit_normalization(smap_proposal* p, const float* feat,
 
 static smap_status forward_checked(smap_proposal* p, const float* feat, long rows, float* disp, uint64_t wait_ns,
                                    int stall) {
+    NvtxRange nvtx_("smap_proposal_forward");
     if (!p || !feat || !disp || rows < 1) return SMAP_E_INVAL;
     smap_status s = launch_forward(p, feat, nullptr, rows, false, nullptr, disp, p->stream, nullptr, wait_ns, stall);
     if (s) return s;
@@ -854,6 +855,7 @@ smap_status smap_proposal_loss_grad(smap_proposal* p, const float* feat, const f
 
 smap_status smap_proposal_train(smap_proposal* p, const float* feat, const float* targ, long n_rows, int steps,
                                 int batch, double lr, double lr_final, float* loss_curve) {
+    NvtxRange nvtx_("smap_proposal_train");
     if (!p || !feat || !targ || n_rows < 1 || steps < 0 || batch < 1) return SMAP_E_INVAL;
     smap_status s = ensure_scratch(p, batch);
     if (s) return s;

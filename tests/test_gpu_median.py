@@ -73,12 +73,13 @@ def test_duplicated_particles_take_the_radix_select(oracle):
 
 
 def test_far_outliers_defeat_the_guess(oracle):
-    """The 32 particles that the first median guess pairs with others sit 100
-    units from the rest, each in its own direction (so every pair distance
-    that involves one of them is far above the median): the guess (a mean of
-    those pair distances) is more than 4 octaves above the median, the
-    histogram around it cannot locate the middle ranks, and the radix select
-    takes over; the next iteration brackets the exact median.
+    """The 32 particles that the first median guess pairs with others sit 10
+    units (100 process-noise standard deviations) from the rest, each in its
+    own direction (so every pair distance that involves one of them is far
+    above the median): the guess (a mean of those pair distances) is more than
+    4 octaves above the median, the histogram around it cannot locate the
+    middle ranks, and the radix select takes over; the next iteration
+    brackets the exact median.
 
     (Pair distances are formed as |x_i|^2 + |x_k|^2 - 2 x_i . x_k in FP32, so
     a tight cluster far from the centre of the set gets distances with an
@@ -87,8 +88,8 @@ def test_far_outliers_defeat_the_guess(oracle):
     wl, t, xprev, xinit = _range_sets(256, 3)
     far = (7 * np.arange(32)) % 256
     ang = 2.0 * np.pi * np.arange(32) / 32.0
-    xinit[:, far, 0] += (100.0 * np.cos(ang)).astype(np.float32)
-    xinit[:, far, 1] += (100.0 * np.sin(ang)).astype(np.float32)
+    xinit[:, far, 0] += (10.0 * np.cos(ang)).astype(np.float32)
+    xinit[:, far, 1] += (10.0 * np.sin(ang)).astype(np.float32)
     c = _run(oracle, wl, t, xprev, xinit, 2)
     assert c[2] == wl.B and c[0] == wl.B
 
