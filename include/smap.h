@@ -374,6 +374,12 @@ smap_status smap_debug_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3
 smap_status smap_debug_normals(uint64_t seed, uint32_t seq, uint32_t t, uint32_t i0,
                                int n, int d, float* normals);
 
+/* The double-float functions the recursion's scores use (about 48-bit
+ * results computed on the FP32 pipe): fn 0 exp (|x| < 80), 1 log (x > 0
+ * normal), 2 sqrt (x > 0), of n FP64 inputs (each split into an FP32 pair),
+ * returned as FP64. Host arrays; synchronous. */
+smap_status smap_debug_df(int fn, const double* in, int n, double* out);
+
 /* Device times of the last smap_run_batch, in milliseconds, from CUDA events
  * recorded on the handle's stream inside its graph: seq_kernel_ms around the
  * persistent step kernel alone, batch_ms around the whole device work (state

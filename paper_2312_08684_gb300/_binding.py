@@ -35,7 +35,7 @@ EXPORTS = [
     "smap_proposal_set_weights", "smap_proposal_fit_normalization", "smap_proposal_forward",
     "smap_proposal_loss_grad", "smap_proposal_train", "smap_proposal_last_error", "smap_proposal_capture",
     "smap_set_proposal", "smap_pf_run_batch", "smap_debug_proposal_forward", "smap_debug_record_learned_init",
-    "smap_state_size", "smap_save", "smap_load",
+    "smap_state_size", "smap_save", "smap_load", "smap_debug_df",
 ]
 MLP_IN_P, MLP_OUT_P, MLP_H = 32, 16, 256
 
@@ -118,6 +118,7 @@ def load():
     L.smap_debug_proposal_forward.argtypes = [_VP, _VP, ctypes.c_long, _VP, ctypes.c_uint64, _I]
     L.smap_debug_record_learned_init.argtypes = [_VP, _VP]
     L.smap_state_size.argtypes = [_VP, ctypes.POINTER(ctypes.c_size_t)]
+    L.smap_debug_df.argtypes = [_I, _VP, _I, _VP]
     L.smap_save.argtypes = [_VP, _VP, ctypes.c_size_t]
     L.smap_load.argtypes = [_VP, _VP, ctypes.c_size_t]
     L.smap_viterbi_noalloc.argtypes = [_I, ctypes.POINTER(ctypes.c_double), _I, _I, _I, _I,
@@ -350,6 +351,14 @@ def smap_debug_normals(seed, seq, t, i0, n, d):
     out = np.empty((int(n), int(d)), np.float32)
     _check(load().smap_debug_normals(ctypes.c_uint64(int(seed)), int(seq), int(t), int(i0), int(n),
                                      int(d), ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def smap_debug_df(fn, x):
+    """Double-float exp (0), log (1) or sqrt (2) of float64 inputs, on the device."""
+    x = np.ascontiguousarray(x, np.float64).ravel()
+    out = np.empty_like(x)
+    _check(load().smap_debug_df(int(fn), ctypes.c_void_p(x.ctypes.data), len(x), ctypes.c_void_p(out.ctypes.data)))
     return out
 
 

@@ -96,6 +96,17 @@ __global__ void philox_kernel(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3
     for (int e = 0; e < 4; ++e) out[(size_t)k * 4 + e] = w[e];
 }
 
+// Double-float exp (fn 0), log (1), sqrt (2) of FP64 inputs split into (hi, lo).
+__global__ void df_kernel(int fn, const double* in, int n, double* out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double v = in[k];
+    const float hi = (float)v;
+    const df::F a = df::make(hi, (float)(v - (double)hi));
+    const df::F r = fn == 0 ? df::exp(a) : fn == 1 ? df::log(a) : df::sqrt(a);
+    out[k] = df::to_double(r);
+}
+
 template <int D>
 __global__ void normals_kernel(uint64_t seed, uint32_t seq, uint32_t t, uint32_t i0, int n, float* out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -203,6 +214,12 @@ bool make_model(int kind, const double* p, int np, ModelParams& mp, std::string&
         err = "unknown model";
         return false;
     }
+    // model constants the double-float paths read: -1/(2 r) of the Gaussian
+    // observation noise (range, zero-velocity range, clutter, linear models)
+    if (kind == SMAP_MODEL_RANGE_CV2D || kind == SMAP_MODEL_CLUTTER_CV2D || kind == SMAP_MODEL_LINEAR_GAUSS)
+        mp.aux[4] = -0.5 / p[5];
+    else if (kind == SMAP_MODEL_RANGE_ZV2D)
+        mp.aux[4] = -0.5 / p[2];
     mp.logtrans_c = 0.0;
     for (int c = 0; c < mp.d; ++c) {
         if (!(mp.q[c] > 0) || !std::isfinite(mp.q[c])) { err = "process noise variances must be finite and > 0"; return false; }
@@ -212,6 +229,15 @@ bool make_model(int kind, const double* p, int np, ModelParams& mp, std::string&
         mp.qinv_f[c] = (float)mp.qinv[c];
         mp.sqrt_qinv_f[c] = (float)mp.sqrt_qinv[c];
         mp.logtrans_c += -0.5 * std::log(two_pi * mp.q[c]);
+    }
+    auto lo = [](double v) { return (float)(v - (double)(float)v); };
+    for (int k = 0; k < np; ++k) mp.pl[k] = lo(p[k]);
+    for (int c = 0; c < mp.d; ++c) mp.qinv_lo[c] = lo(mp.qinv[c]);
+    mp.ltc[0] = (float)mp.logtrans_c;
+    mp.ltc[1] = lo(mp.logtrans_c);
+    for (int k = 0; k < 8; ++k) {
+        mp.auxh[k] = (float)mp.aux[k];
+        mp.auxl[k] = lo(mp.aux[k]);
     }
     return true;
 }
@@ -1327,6 +1353,20 @@ smap_status smap_debug_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3
     g_launches.fetch_add(1);
     cudaError_t e = cudaMemcpy(out, d, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost);
     cudaFree(d);
+    return e == cudaSuccess ? SMAP_OK : SMAP_E_CUDA;
+}
+
+smap_status smap_debug_df(int fn, const double* in, int n, double* out) {
+    if (fn < 0 || fn > 2 || n < 1 || !in || !out) return SMAP_E_INVAL;
+    double* dv = nullptr;
+    if (cudaMalloc(&dv, sizeof(double) * 2 * n) != cudaSuccess) return SMAP_E_NOMEM;
+    cudaError_t e = cudaMemcpy(dv, in, sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        df_kernel<<<(n + 255) / 256, 256>>>(fn, dv, n, dv + n);
+        g_launches.fetch_add(1);
+        e = cudaMemcpy(out, dv + n, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    }
+    cudaFree(dv);
     return e == cudaSuccess ? SMAP_OK : SMAP_E_CUDA;
 }
 

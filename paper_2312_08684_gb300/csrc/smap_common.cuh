@@ -27,6 +27,12 @@ struct ModelParams {
     double logtrans_c;        // -1/2 sum_d log(2 pi q_d)
     double aux[8];            // model-specific constants (see smap_models.cuh)
     float auxf[8];
+    // double-float (hi, lo) forms of the FP64 constants: p = pf + pl,
+    // qinv = qinv_f + qinv_lo, logtrans_c = ltc[0] + ltc[1], aux = auxh + auxl
+    float pl[kMaxParams];
+    float qinv_lo[kMaxD];
+    float ltc[2];
+    float auxh[8], auxl[8];
 };
 
 // Per-launch arguments of the sequence kernel.

@@ -1069,12 +1069,17 @@ __device__ __forceinline__ double trans_m64(const ModelParams& mp, const float* 
 // of every other j, v1 - v2 > 2 e_j1 + 2 E_i proves j1 the unique maximum of
 // S (and of its FP64 evaluation). Otherwise (a near-tie) every j with
 // v_ij >= v1 - 2 e_j1 - 2 E_i is evaluated in FP64, lowest j first.
+// FP64 scores: phi_t(i) = log p(z_t | x_i) + log p(x_i | x_{t-1}^j) +
+// phi_{t-1}(j), accumulated in FP64. The two log-density terms are evaluated
+// in double-float arithmetic (about 48 bits, on the FP32 pipe) where the model
+// provides it and the previous set xprev (FP32, global [Np][D]) is given;
+// otherwise in FP64 from the FP64 transition means f64.
 // On return: best[p], phinew[p] for the block's particles. fs is overwritten
 // (g_j replaces f~_j).
 // ---------------------------------------------------------------------------
 template <class M, int PPT>
 __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, const double* f64,
-                             int* best, double* phinew) {
+                             const float* xprev, int* best, double* phinew) {
     constexpr int D = M::D, DP = M::DP;
     const int tid = threadIdx.x, NT = blockDim.x;
     constexpr float u = 5.9604644775390625e-08f;   // 2^-24
@@ -1162,6 +1167,16 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
         uniq[p] = (v1[p] - v2[p]) > m;
         thr[p] = v1[p] - m;
     }
+    // log p(x_i | x_{t-1}^j) of the particle at row r of xs
+    auto logtrans = [&](int r, int j) -> double {
+        if constexpr (M::kTransDF) {
+            if (xprev) {
+                const df::F q = M::trans_sq_df(mp, s.xs + r, xprev + (size_t)j * D);
+                return df::to_double(df::add(df::make(mp.ltc[0], mp.ltc[1]), df::scale2(q, -0.5f)));
+            }
+        }
+        return mp.logtrans_c - 0.5 * trans_m64<D>(mp, s.xs + r, f64 + (size_t)j * D);
+    };
     double bs[PPT], blt[PPT];
     int row[PPT];
     bool multi = false;
@@ -1173,7 +1188,7 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
         best[p] = 0;
         if (uniq[p]) {
             const int j = j1[p];
-            blt[p] = mp.logtrans_c - 0.5 * trans_m64<D>(mp, s.xs + row[p], f64 + (size_t)j * D);
+            blt[p] = logtrans(row[p], j);
             bs[p] = s.phis[j] + blt[p];
             best[p] = j;
         } else {
@@ -1193,7 +1208,7 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
 #pragma unroll
                 for (int c = 0; c < D; ++c) v = fmaf(xc[p][c], gj[c], v);
                 if (v >= thr[p]) {
-                    const double lt = mp.logtrans_c - 0.5 * trans_m64<D>(mp, s.xs + row[p], f64 + (size_t)j * D);
+                    const double lt = logtrans(row[p], j);
                     const double sv = s.phis[j] + lt;
                     if (sv > bs[p]) { bs[p] = sv; blt[p] = lt; best[p] = j; }
                 }
@@ -1205,7 +1220,7 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
         if (bs[p] == -INFINITY) {
             // no candidate passed the screen (non-finite inputs): plain FP64 scan
             for (int j = 0; j < Np; ++j) {
-                const double lt = mp.logtrans_c - 0.5 * trans_m64<D>(mp, s.xs + row[p], f64 + (size_t)j * D);
+                const double lt = logtrans(row[p], j);
                 const double sv = s.phis[j] + lt;
                 if (sv > bs[p]) { bs[p] = sv; blt[p] = lt; best[p] = j; }
             }
@@ -1213,7 +1228,7 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
                 // no finite candidate at all: predecessor 0, scored with its
                 // own (non-finite) transition term, so the score is not finite
                 best[p] = 0;
-                blt[p] = mp.logtrans_c - 0.5 * trans_m64<D>(mp, s.xs + row[p], f64);
+                blt[p] = logtrans(row[p], 0);
             }
         }
     }
@@ -1221,10 +1236,16 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
     for (int p = 0; p < PPT; ++p) {
         const int i = tid + p * NT;
         if (i >= N) { phinew[p] = 0.0; continue; }
-        double xd[D];
+        double ll;
+        if constexpr (M::kLikDF) {
+            ll = df::to_double(M::loglik_df(mp, s.zs, s.xs + row[p]));
+        } else {
+            double xd[D];
 #pragma unroll
-        for (int c = 0; c < D; ++c) xd[c] = (double)s.xs[row[p] + c];
-        phinew[p] = M::loglik64(mp, s.zs, xd) + blt[p] + s.phis[best[p]];
+            for (int c = 0; c < D; ++c) xd[c] = (double)s.xs[row[p] + c];
+            ll = M::loglik64(mp, s.zs, xd);
+        }
+        phinew[p] = ll + blt[p] + s.phis[best[p]];
     }
 }
 
@@ -1297,7 +1318,8 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
             }
             int best[PPT];
             double phinew[PPT];
-            viterbi_step<M, PPT>(mp, s, N, Np, f64, best, phinew);
+            const float* xprev = (t >= 2) ? a.hist + (((size_t)b * a.maxT + (t - 2)) * a.Nmax) * D : nullptr;
+            viterbi_step<M, PPT>(mp, s, N, Np, f64, xprev, best, phinew);
             __syncthreads();   // all reads of phis / xs done
             bool bad = false;
             float* dst = a.hist + (((size_t)b * a.maxT + (t - 1)) * a.Nmax) * D;

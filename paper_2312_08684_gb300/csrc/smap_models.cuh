@@ -7,18 +7,49 @@
 //   transition64(mp, sc, x, f)      the same in FP64
 //   grad_loglik(mp, z, x, g)        grad_x log p(z | x) in FP32 (Eq. SSM-z)
 //   loglik64(mp, z, x)              log p(z | x) in FP64, full normaliser
+// and, where kTransDF / kLikDF say so, the same terms in double-float
+// arithmetic (about 48 bits, on the FP32 pipe) from the FP32 particles:
+//   trans_sq_df(mp, x, xp)          |x - f_t(xp)|^2_{Q^-1}, the residual formed
+//                                   from x and the previous particle xp
+//   loglik_df(mp, z, x)             log p(z | x)
 // Parameter layouts are documented in include/smap.h; aux[] holds constants
-// the host precomputes in FP64 (listed per model).
+// the host precomputes in FP64 (listed per model; aux[4] = -1/(2 r) for the
+// Gaussian-noise models that have a double-float likelihood).
 #pragma once
 
 #include "smap_common.cuh"
+#include "smap_df.cuh"
 
 namespace smap {
+
+__device__ __forceinline__ df::F dfp(const ModelParams& mp, int k) { return df::make(mp.pf[k], mp.pl[k]); }
+__device__ __forceinline__ df::F dfaux(const ModelParams& mp, int k) { return df::make(mp.auxh[k], mp.auxl[k]); }
+__device__ __forceinline__ df::F dfqinv(const ModelParams& mp, int c) { return df::make(mp.qinv_f[c], mp.qinv_lo[c]); }
+// (x - xp) exactly, as a double-float
+__device__ __forceinline__ df::F df_diff(float x, float xp) { return df::two_sum(x, -xp); }
+// log-density sum over heard range measurements: sum_l [aux0 - (z_l - |p - b_l|)^2 / (2 r)],
+// beacon l at parameters (k0 + 2 l, k0 + 2 l + 1)
+__device__ __forceinline__ df::F range_loglik_df(const ModelParams& mp, const float* z, const float* x, int nb,
+                                                 int k0) {
+    df::F s = df::make(0.0f, 0.0f);
+    int heard = 0;
+    for (int l = 0; l < nb; ++l) {
+        const float zl = z[l];
+        if (zl != zl) continue;
+        const df::F dx = df::sub(df::make(x[0], 0.0f), dfp(mp, k0 + 2 * l));
+        const df::F dy = df::sub(df::make(x[1], 0.0f), dfp(mp, k0 + 2 * l + 1));
+        const df::F rho = df::sqrt(df::add(df::sqr(dx), df::sqr(dy)));
+        s = df::add(s, df::sqr(df::sub(df::make(zl, 0.0f), rho)));
+        ++heard;
+    }
+    return df::add(df::mul(s, dfaux(mp, 4)), df::mul_f(dfaux(mp, 0), (float)heard));
+}
 
 // 1-D nonstationary growth model. p = [a, b, c, omega, t_off, q, r, hcoef].
 // aux[0] = -1/2 log(2 pi r), auxf[0] = 1/r.
 struct ModelNGM1D {
     static constexpr int KIND = 1, D = 1, DP = 1, DY = 1;
+    static constexpr bool kTransDF = false, kLikDF = false;
     __device__ static double step_const(const ModelParams& mp, int t) {
         return mp.p[2] * cos(mp.p[3] * ((double)t + mp.p[4]));
     }
@@ -57,6 +88,19 @@ struct CVTransition {
         f[2] = x[2];
         f[3] = x[3];
     }
+    // position residual (x - xp) - dt vp, velocity residual v - vp
+    __device__ static df::F trans_sq_df(const ModelParams& mp, const float* x, const float* xp) {
+        const df::F dt = dfp(mp, 0);
+        df::F s = df::make(0.0f, 0.0f);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const df::F e = df::sub(df_diff(x[c], xp[c]), df::mul_f(dt, xp[c + 2]));
+            s = df::add(s, df::mul(df::sqr(e), dfqinv(mp, c)));
+        }
+#pragma unroll
+        for (int c = 2; c < 4; ++c) s = df::add(s, df::mul(df::sqr(df_diff(x[c], xp[c])), dfqinv(mp, c)));
+        return s;
+    }
 };
 
 // Section V-C's target without a motion prior: x = (px, py), zero-velocity
@@ -65,6 +109,14 @@ struct CVTransition {
 // aux[0] = -1/2 log(2 pi r), auxf[0] = 1/r.
 struct ModelRangeZV {
     static constexpr int KIND = 6, D = 2, DP = 2, DY = 8;
+    static constexpr bool kTransDF = true, kLikDF = true;
+    __device__ static df::F trans_sq_df(const ModelParams& mp, const float* x, const float* xp) {
+        return df::add(df::mul(df::sqr(df_diff(x[0], xp[0])), dfqinv(mp, 0)),
+                       df::mul(df::sqr(df_diff(x[1], xp[1])), dfqinv(mp, 1)));
+    }
+    __device__ static df::F loglik_df(const ModelParams& mp, const float* z, const float* x) {
+        return range_loglik_df(mp, z, x, (int)mp.p[3], 4);
+    }
     __device__ static double step_const(const ModelParams&, int) { return 0.0; }
     __device__ static void transition(const ModelParams&, double, const float* x, float* f) {
         f[0] = x[0];
@@ -114,6 +166,7 @@ struct ModelRangeZV {
 // auxf[4] = 1/rr, auxf[5] = 1/rb.
 struct ModelSE2RB {
     static constexpr int KIND = 7, D = 3, DP = 4, DY = 2;
+    static constexpr bool kTransDF = false, kLikDF = false;
     __device__ static double step_const(const ModelParams&, int) { return 0.0; }
     __device__ static void transition(const ModelParams& mp, double, const float* x, float* f) {
         const float th = x[2] + mp.auxf[1];
@@ -189,6 +242,10 @@ struct ModelSE2RB {
 // aux[0] = -1/2 log(2 pi r), auxf[0] = 1/r. NaN observation = beacon not heard.
 struct ModelRangeCV : CVTransition {
     static constexpr int KIND = 2, D = 4, DP = 4, DY = 8;
+    static constexpr bool kTransDF = true, kLikDF = true;
+    __device__ static df::F loglik_df(const ModelParams& mp, const float* z, const float* x) {
+        return range_loglik_df(mp, z, x, (int)mp.p[6], 7);
+    }
     __device__ static void grad_loglik(const ModelParams& mp, const float* z, const float* x, float* g) {
         const int nb = (int)mp.p[6];
         float g0 = 0.0f, g1 = 0.0f;
@@ -223,6 +280,40 @@ struct ModelRangeCV : CVTransition {
 // auxf[0] = 1/r, auxf[1] = aux[0] * log2(e), auxf[2] = aux[1] * log2(e).
 struct ModelClutterCV : CVTransition {
     static constexpr int KIND = 3, D = 4, DP = 4, DY = 64;
+    static constexpr bool kTransDF = true, kLikDF = true;
+    // The same mixture in double-float: the FP32 pass finds the largest term
+    // (its value shifts the sum: the result does not depend on the shift) and
+    // the terms within 45 nats of it; the shifted sum s >= 1 and its log are
+    // double-float (the largest term contributes exp(0) = 1 exactly).
+    __device__ static df::F loglik_df(const ModelParams& mp, const float* z, const float* x) {
+        if (!(isfinite(x[0]) && isfinite(x[1]))) return df::make(__int_as_float(0x7fc00000), 0.0f);
+        const int M = (int)mp.p[6];
+        const float c2 = -0.5f * mp.auxf[0];
+        const float a0f = mp.auxh[0], a1f = mp.auxh[1];
+        float mxf = a1f;
+        int mi = -1;   // -1: the outlier term is the largest
+        for (int m = 0; m < M; ++m) {
+            const float ex = z[2 * m] - x[0], ey = z[2 * m + 1] - x[1];
+            const float a = fmaf(c2, fmaf(ex, ex, ey * ey), a0f);
+            if (a > mxf) { mxf = a; mi = m; }
+        }
+        const float keep = mxf - 45.0f;
+        const df::F c = dfaux(mp, 4);
+        auto term = [&](int m) {
+            const df::F ex = df_diff(z[2 * m], x[0]), ey = df_diff(z[2 * m + 1], x[1]);
+            return df::add(dfaux(mp, 0), df::mul(df::add(df::sqr(ex), df::sqr(ey)), c));
+        };
+        const df::F mx = mi < 0 ? dfaux(mp, 1) : term(mi);
+        df::F s = df::make(1.0f, 0.0f);
+        if (mi >= 0 && a1f >= keep) s = df::add(s, df::exp(df::sub(dfaux(mp, 1), mx)));
+        for (int m = 0; m < M; ++m) {
+            if (m == mi) continue;
+            const float ex = z[2 * m] - x[0], ey = z[2 * m + 1] - x[1];
+            if (!(fmaf(c2, fmaf(ex, ex, ey * ey), a0f) >= keep)) continue;
+            s = df::add(s, df::exp(df::sub(term(m), mx)));
+        }
+        return df::add(mx, df::log(s));
+    }
     __device__ static void grad_loglik(const ModelParams& mp, const float* z, const float* x, float* g) {
         const int M = (int)mp.p[6];
         const float rinv = mp.auxf[0];
@@ -285,6 +376,19 @@ struct ModelClutterCV : CVTransition {
 template <int NL>
 struct ModelPlanarArm {
     static constexpr int KIND = 4, D = 2 * NL, DP = (2 * NL + 3) & ~3, DY = 2;
+    static constexpr bool kTransDF = true, kLikDF = false;
+    // angle residual (th - thp) - dt wp, rate residual w - wp
+    __device__ static df::F trans_sq_df(const ModelParams& mp, const float* x, const float* xp) {
+        const df::F dt = dfp(mp, 0);
+        df::F s = df::make(0.0f, 0.0f);
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const df::F e = df::sub(df_diff(x[k], xp[k]), df::mul_f(dt, xp[NL + k]));
+            s = df::add(s, df::mul(df::sqr(e), dfqinv(mp, k)));
+            s = df::add(s, df::mul(df::sqr(df_diff(x[NL + k], xp[NL + k])), dfqinv(mp, NL + k)));
+        }
+        return s;
+    }
     __device__ static double step_const(const ModelParams&, int) { return 0.0; }
     __device__ static void transition(const ModelParams& mp, double, const float* x, float* f) {
         const float dt = mp.pf[0];
@@ -346,6 +450,11 @@ struct ModelPlanarArm {
 // aux[0] = -log(2 pi r), auxf[0] = 1/r.
 struct ModelLinearGauss : CVTransition {
     static constexpr int KIND = 5, D = 4, DP = 4, DY = 2;
+    static constexpr bool kTransDF = true, kLikDF = true;
+    __device__ static df::F loglik_df(const ModelParams& mp, const float* z, const float* x) {
+        const df::F q = df::add(df::sqr(df_diff(z[0], x[0])), df::sqr(df_diff(z[1], x[1])));
+        return df::add(dfaux(mp, 0), df::mul(q, dfaux(mp, 4)));
+    }
     __device__ static void grad_loglik(const ModelParams& mp, const float* z, const float* x, float* g) {
         g[0] = (z[0] - x[0]) * mp.auxf[0];
         g[1] = (z[1] - x[1]) * mp.auxf[0];
