@@ -227,6 +227,7 @@ def all_configs(args):
     pk, src = peaks()
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     peak = alu_peak_gops(pk.get("sm_max_mhz", 2070.0), sms)
+    abi_grid = {}
     for name, (mk, desc, t_sample, _) in CONFIGS.items():
         wl = make_workload(name, 0)
         stream = torch.cuda.Stream()
@@ -251,6 +252,7 @@ def all_configs(args):
                 run()
             ms = timed(run, args.steps)
             kms = abi.smap_last_kernel_ms(est.h)[0]
+            abi_grid[name] = abi.smap_get_variant(est.h)
             hist = torch.empty((wl.B, wl.maxT, wl.N, wl.d), dtype=torch.float32, device="cuda")
             abi.smap_get_history(est.h, hist)
             vit = lambda: abi.smap_viterbi(est.h, hist, y, wl.T, wl.Nseq, path, J)
@@ -260,12 +262,18 @@ def all_configs(args):
         units = wl.particle_updates()
         ach = algorithmic_ops(wl) / (kms / 1000.0) / 1e9
         vach = recursion_ops(wl) / (vms / 1000.0) / 1e9
+        # fewer sequences than SMs: one block per sequence, so the SMs the
+        # launch occupies bound it, not the whole GPU
+        _, _, grid = abi_grid[name] if name in abi_grid else (0, 0, sms)
+        occ_sms = max(1, min(sms, grid))
+        peak_occ = alu_peak_gops(pk.get("sm_max_mhz", 2070.0), occ_sms)
         line = {"config": name, "workload": desc, "B": wl.B, "N": wl.N, "d": wl.d, "L": wl.L,
                 "T": f"{int(wl.T.min())}..{int(wl.T.max())}" if wl.T.min() != wl.T.max() else int(wl.T[0]),
                 "metric": METRIC, "value": units / (ms / 1000.0), "unit": UNIT, "ms_per_batch": ms,
                 "sequences_per_s": wl.B / (ms / 1000.0),
                 "roofline": {"bound": "alu", "kernel": "seq_kernel", "kernel_ms": kms, "achieved": ach,
-                             "peak": peak, "unit": "Gop/s", "frac": ach / peak},
+                             "peak": peak, "unit": "Gop/s", "frac": ach / peak, "occupied_sms": occ_sms,
+                             "frac_of_occupied_sms": ach / peak_occ},
                 "viterbi": {"ms": vms, "achieved": vach, "frac": vach / peak, "unit": "Gop/s"},
                 "cpu_baseline": cpu_baseline(wl, os.cpu_count() or 1, t_sample)}
         print(json.dumps(line), flush=True)

@@ -374,8 +374,18 @@ smap_status smap_debug_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3
 smap_status smap_debug_normals(uint64_t seed, uint32_t seq, uint32_t t, uint32_t i0,
                                int n, int d, float* normals);
 
+/* Debug build only (compiled with SMAP_DEBUG, where every shared-memory row
+ * access and the global sequence / step / particle indices are checked, a
+ * failed check is recorded and the access skipped, and the calls that launch
+ * the kernels return SMAP_E_INVAL naming the failed check): one checked row
+ * load at `index` from a shared array of `rows` rows (1..1024) filled with
+ * 1.0. value receives what the load returned (1.0, or 0.0 when the check
+ * failed), code and at the failed check's code (0: none; 1: a row index)
+ * and index. Other builds return SMAP_E_UNSUPPORTED. */
+smap_status smap_debug_bounds_probe(int rows, int index, float* value, int* code, int* at);
+
 /* The double-float functions the recursion's scores use (about 48-bit
- * results computed on the FP32 pipe): fn 0 exp (|x| < 80), 1 log (x > 0
+ * results computed on the FP32 pipe): fn 0 exp (|x| < 60), 1 log (x > 0
  * normal), 2 sqrt (x > 0), of n FP64 inputs (each split into an FP32 pair),
  * returned as FP64. Host arrays; synchronous. */
 smap_status smap_debug_df(int fn, const double* in, int n, double* out);

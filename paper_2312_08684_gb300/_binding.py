@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_build", "libsmap.so")
+# SMAP_LIBRARY may name another build of the library (the bounds-checked
+# debug build, paper_2312_08684_gb300/_build_debug/libsmap_debug.so).
+LIB_PATH = os.environ.get("SMAP_LIBRARY") or os.path.join(_PKG, "_build", "libsmap.so")
 
 SMAP_OK, SMAP_E_INVAL, SMAP_E_NOMEM, SMAP_E_CUDA, SMAP_E_STATE, SMAP_E_TIMEOUT, \
     SMAP_E_NONFINITE, SMAP_E_UNSUPPORTED = range(8)
@@ -35,7 +37,7 @@ EXPORTS = [
     "smap_proposal_set_weights", "smap_proposal_fit_normalization", "smap_proposal_forward",
     "smap_proposal_loss_grad", "smap_proposal_train", "smap_proposal_last_error", "smap_proposal_capture",
     "smap_set_proposal", "smap_pf_run_batch", "smap_debug_proposal_forward", "smap_debug_record_learned_init",
-    "smap_state_size", "smap_save", "smap_load", "smap_debug_df",
+    "smap_state_size", "smap_save", "smap_load", "smap_debug_df", "smap_debug_bounds_probe",
 ]
 MLP_IN_P, MLP_OUT_P, MLP_H = 32, 16, 256
 
@@ -119,6 +121,7 @@ def load():
     L.smap_debug_record_learned_init.argtypes = [_VP, _VP]
     L.smap_state_size.argtypes = [_VP, ctypes.POINTER(ctypes.c_size_t)]
     L.smap_debug_df.argtypes = [_I, _VP, _I, _VP]
+    L.smap_debug_bounds_probe.argtypes = [_I, _I, _VP, _VP, _VP]
     L.smap_save.argtypes = [_VP, _VP, ctypes.c_size_t]
     L.smap_load.argtypes = [_VP, _VP, ctypes.c_size_t]
     L.smap_viterbi_noalloc.argtypes = [_I, ctypes.POINTER(ctypes.c_double), _I, _I, _I, _I,
@@ -352,6 +355,15 @@ def smap_debug_normals(seed, seq, t, i0, n, d):
     _check(load().smap_debug_normals(ctypes.c_uint64(int(seed)), int(seq), int(t), int(i0), int(n),
                                      int(d), ctypes.c_void_p(out.ctypes.data)))
     return out
+
+
+def smap_debug_bounds_probe(rows, index):
+    """Debug build only: (value loaded, failed-check code, index) of one checked row load."""
+    v = np.zeros(1, np.float32)
+    c = np.zeros(2, np.int32)
+    _check(load().smap_debug_bounds_probe(int(rows), int(index), ctypes.c_void_p(v.ctypes.data),
+                                          ctypes.c_void_p(c.ctypes.data), ctypes.c_void_p(c[1:].ctypes.data)))
+    return float(v[0]), int(c[0]), int(c[1])
 
 
 def smap_debug_df(fn, x):

@@ -96,6 +96,22 @@ __global__ void philox_kernel(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3
     for (int e = 0; e < 4; ++e) out[(size_t)k * 4 + e] = w[e];
 }
 
+#ifdef SMAP_DEBUG
+// Debug build: one checked row load from a shared array of `rows` rows filled
+// with 1; out = {code, index} of the failed check (or 0), then the loaded value.
+__global__ void bounds_probe_kernel(int rows, int index, int* out) {
+    extern __shared__ __align__(16) float probe_sm[];
+    SMAP_DBG_BEGIN(rows, out);
+    for (int e = threadIdx.x; e < 4 * rows; e += blockDim.x) probe_sm[e] = 1.0f;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float r[4];
+        load_row<4, 4>(probe_sm, index, r);
+        out[2] = __float_as_int(r[0]);
+    }
+}
+#endif
+
 // Double-float exp (fn 0), log (1), sqrt (2) of FP64 inputs split into (hi, lo).
 __global__ void df_kernel(int fn, const double* in, int n, double* out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -433,6 +449,7 @@ smap_status launch_seq(smap_handle* h, int v, int items, int mode, const float* 
     a.y_full = opts.y_full;
     a.skip_done = opts.skip_done;
     a.seq_base = opts.seq_base;
+    a.Btot = h->B;
     if (opts.L >= 0) a.L = opts.L;
     void* args[] = {&a};
     cudaStream_t ls = opts.stream ? opts.stream : h->stream;
@@ -474,6 +491,9 @@ smap_status collect_status(smap_handle* h) {
     SMAP_CUDA(h, cudaStreamSynchronize(h->stream));
     if (st[h->B + 4] != 0)
         return fail(h, SMAP_E_TIMEOUT, "learned proposal: a bounded wait of the tensor-core network kernel ran out");
+    if (st[h->B + kDbgWord] != 0)
+        return fail(h, SMAP_E_INVAL, "debug build: bounds check " + std::to_string(st[h->B + kDbgWord]) +
+                                         " failed at index " + std::to_string(st[h->B + kDbgWord + 1]));
     for (int b = 0; b < h->B; ++b) {
         if (st[b] == SMAP_E_NONFINITE)
             return fail(h, SMAP_E_NONFINITE, "sequence " + std::to_string(b) + ": particles or scores became non-finite");
@@ -1326,8 +1346,8 @@ smap_status smap_debug_svgd(smap_handle* h, int t, const float* x_prev, int n_pr
     a.eps = (float)h->cfg.step; a.bw_value = (float)h->cfg.bw_value;
     a.xprev = dxp; a.x0 = h->x0; a.xinit = dxi; a.y = dy; a.xout = dxo; a.hout = dho; a.f64 = df;
     a.phiprev = dph;
-    a.stats = h->status + h->B;   // the median counters count this call alone
-    e = cudaMemsetAsync(a.stats, 0, sizeof(int) * 4, h->stream);
+    a.stats = h->status + h->B;   // the median counters (and the debug word) count this call alone
+    e = cudaMemsetAsync(a.stats, 0, sizeof(int) * kStatusExtra, h->stream);
     if (e != cudaSuccess) { cleanup(); return cuda_fail(h, e, "debug_svgd"); }
     const int v = h->variant >= 0 ? h->variant : heuristic_variant(h);
     const int nt = variant_threads(v, h->Nmax);
@@ -1339,8 +1359,13 @@ smap_status smap_debug_svgd(smap_handle* h, int t, const float* x_prev, int n_pr
     g_launches.fetch_add(1);
     if (e == cudaSuccess) e = cudaMemcpy(x_out, dxo, sizeof(float) * B * N * d, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && h_out && n_iters > 0) e = cudaMemcpy(h_out, dho, sizeof(float) * B * n_iters, cudaMemcpyDeviceToHost);
+    int dbg[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(dbg, h->status + h->B + kDbgWord, sizeof(dbg), cudaMemcpyDeviceToHost);
     cleanup();
     if (e != cudaSuccess) return cuda_fail(h, e, "debug_svgd");
+    if (dbg[0] != 0)
+        return fail(h, SMAP_E_INVAL, "debug build: bounds check " + std::to_string(dbg[0]) + " failed at index " +
+                                         std::to_string(dbg[1]));
     return SMAP_OK;
 }
 
@@ -1354,6 +1379,31 @@ smap_status smap_debug_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3
     cudaError_t e = cudaMemcpy(out, d, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost);
     cudaFree(d);
     return e == cudaSuccess ? SMAP_OK : SMAP_E_CUDA;
+}
+
+smap_status smap_debug_bounds_probe(int rows, int index, float* value, int* code, int* at) {
+#ifdef SMAP_DEBUG
+    if (rows < 1 || rows > 1024 || !value || !code || !at) return SMAP_E_INVAL;
+    int* dv = nullptr;
+    if (cudaMalloc(&dv, sizeof(int) * 4) != cudaSuccess) return SMAP_E_NOMEM;
+    cudaError_t e = cudaMemset(dv, 0, sizeof(int) * 4);
+    if (e == cudaSuccess) {
+        bounds_probe_kernel<<<1, 32, sizeof(float) * 4 * rows>>>(rows, index, dv);
+        g_launches.fetch_add(1);
+        e = cudaGetLastError();
+    }
+    int hv[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(hv, dv, sizeof(hv), cudaMemcpyDeviceToHost);
+    cudaFree(dv);
+    if (e != cudaSuccess) return SMAP_E_CUDA;
+    *code = hv[0];
+    *at = hv[1];
+    memcpy(value, &hv[2], sizeof(float));
+    return SMAP_OK;
+#else
+    (void)rows; (void)index; (void)value; (void)code; (void)at;
+    return SMAP_E_UNSUPPORTED;
+#endif
 }
 
 smap_status smap_debug_df(int fn, const double* in, int n, double* out) {

@@ -11,7 +11,9 @@ constexpr int kMaxParams = 128;  // model parameter vector length
 constexpr int kMaxDy = 64;       // largest observation dimension
 constexpr int kCandCap = 2048;   // median bracket candidates kept in shared memory
 constexpr int kMaxN = 4096;      // particles per sequence (backpointers are uint16)
-constexpr int kStatusExtra = 5;  // after the B per-sequence status words: 4 median counters, 1 error word
+constexpr int kStatusExtra = 7;  // after the B per-sequence status words: 4 median counters, 1 error word,
+                                 // 2 words of the debug build's first failed bounds check (code, index)
+constexpr int kDbgWord = 5;      // offset of those 2 words after the B status words
 
 // Model constants, passed by value in the kernel parameters (constant bank).
 struct ModelParams {
@@ -62,6 +64,7 @@ struct SeqArgs {
     int y_full;               // mode 1: y is [B][maxT][dy] (indexed by the step)
     int skip_done;            // mode 1: skip sequences with tcur >= Tend
     int seq_base;             // without `order`, item k is sequence seq_base + k
+    int Btot;                 // sequences of the handle's arrays (debug build's bounds checks)
     int kernel;               // Stein kernel: 0 RBF, 1 IMQ, 2 Matern 3/2
 };
 
@@ -81,6 +84,35 @@ struct DebugSvgdArgs {
     int kernel;               // Stein kernel: 0 RBF, 1 IMQ, 2 Matern 3/2
     int* stats;               // median-path counters [4] (see median_sqdist), or null
 };
+
+#ifdef SMAP_DEBUG
+// Debug build (SMAP_DEBUG): the row index of every shared-memory particle
+// array access and the sequence / step / particle indices of the global
+// arrays are checked before the access; a failed check records (code, index)
+// in the launch's debug word (the first failure wins) and the access is
+// skipped: loads return zeros, stores are dropped. Nothing traps.
+__shared__ int g_dbg_rows;    // rows of the shared [rows][DP] arrays of this block
+__shared__ int* g_dbg_word;   // [2] (code, index), or null
+__device__ __forceinline__ bool dbg_check(bool ok, int code, long long index) {
+    if (!ok && g_dbg_word && atomicCAS(g_dbg_word, 0, code) == 0) g_dbg_word[1] = (int)index;
+    return ok;
+}
+// Called by every thread at the start of a kernel that uses the shared rows.
+__device__ __forceinline__ void dbg_begin(int rows, int* word) {
+    if (threadIdx.x == 0) {
+        g_dbg_rows = rows;
+        g_dbg_word = word;
+    }
+    __syncthreads();
+}
+#define SMAP_DBG(ok, code, index) ::smap::dbg_check((ok), (code), (long long)(index))
+#define SMAP_DBG_BEGIN(rows, word) ::smap::dbg_begin((rows), (word))
+#else
+#define SMAP_DBG(ok, code, index) true
+#define SMAP_DBG_BEGIN(rows, word) ((void)0)
+#endif
+// Codes of the debug build's bounds checks.
+enum DbgCode { kDbgRow = 1, kDbgSeq = 2, kDbgStep = 3, kDbgPart = 4, kDbgPrev = 5 };
 
 // ex2.approx: 2^x on the special-function unit (max rel. error ~2^-22).
 __device__ __forceinline__ float fast_exp2(float x) {

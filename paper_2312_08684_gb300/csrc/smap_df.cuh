@@ -100,7 +100,8 @@ __device__ __forceinline__ F sqrt(F a) {
 // p = c + x q in df (one Horner step).
 __device__ __forceinline__ F horner(F q, F x, F c) { return add(mul(q, x), c); }
 
-// exp(t) for -80 < t < 80: t = k ln2 + r with ln 2 split into three parts
+// exp(t) for -60 < t < 60 (further out the low part of the result leaves
+// FP32's normal range): t = k ln2 + r with ln 2 split into three parts
 // (the first exactly multiplied by the integer k, the second by an exact
 // product), |r| <= ln2/2; x = r/2 goes into the Taylor series (orders 7-11 in
 // FP32, where they are below 2^-27 of the sum; orders 0-6 in df), and the

@@ -91,6 +91,13 @@ __device__ inline Sm bind_smem(unsigned char* base, int Nmax, int DP) {
 // Row i of a [*][DP] shared array: 128-bit loads when DP is a multiple of 4.
 template <int D, int DP>
 __device__ __forceinline__ void load_row(const float* base, int i, float* r) {
+#ifdef SMAP_DEBUG
+    if (!SMAP_DBG((unsigned)i < (unsigned)g_dbg_rows, kDbgRow, i)) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) r[c] = 0.0f;
+        return;
+    }
+#endif
     if constexpr (DP % 4 == 0) {
         const float4* p = reinterpret_cast<const float4*>(base + i * DP);
 #pragma unroll
@@ -109,6 +116,7 @@ __device__ __forceinline__ void load_row(const float* base, int i, float* r) {
 
 template <int D, int DP>
 __device__ __forceinline__ void store_row(float* base, int i, const float* r) {
+    if (!SMAP_DBG((unsigned)i < (unsigned)g_dbg_rows, kDbgRow, i)) return;
 #pragma unroll
     for (int c = 0; c < DP; ++c) base[i * DP + c] = c < D ? r[c] : 0.0f;
 }
@@ -1170,7 +1178,7 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
     // log p(x_i | x_{t-1}^j) of the particle at row r of xs
     auto logtrans = [&](int r, int j) -> double {
         if constexpr (M::kTransDF) {
-            if (xprev) {
+            if (xprev && SMAP_DBG(j >= 0 && j < Np, kDbgPrev, j)) {
                 const df::F q = M::trans_sq_df(mp, s.xs + r, xprev + (size_t)j * D);
                 return df::to_double(df::add(df::make(mp.ltc[0], mp.ltc[1]), df::scale2(q, -0.5f)));
             }
@@ -1264,6 +1272,7 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
     constexpr int D = M::D, DP = M::DP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Sm s = bind_smem(smem_raw, a.Nmax, DP);
+    SMAP_DBG_BEGIN(a.Nmax, a.stats ? a.stats + kDbgWord : nullptr);
     const ModelParams& mp = a.mp;
     const int tid = threadIdx.x, NT = blockDim.x;
     __shared__ int s_item;
@@ -1276,6 +1285,7 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
         const int item = s_item;
         if (item >= a.B) break;
         const int b = a.order ? a.order[item] : a.seq_base + item;
+        if (!SMAP_DBG(b >= 0 && b < a.Btot, kDbgSeq, b)) continue;
         if (a.mode == 1 && a.active && !a.active[b]) continue;
         if (a.status[b] != 0) continue;
         const int N = a.Nseq[b];
@@ -1318,6 +1328,7 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
             }
             int best[PPT];
             double phinew[PPT];
+            if (!SMAP_DBG(t >= 1 && t <= a.maxT, kDbgStep, t)) break;
             const float* xprev = (t >= 2) ? a.hist + (((size_t)b * a.maxT + (t - 2)) * a.Nmax) * D : nullptr;
             viterbi_step<M, PPT>(mp, s, N, Np, f64, xprev, best, phinew);
             __syncthreads();   // all reads of phis / xs done
@@ -1364,6 +1375,7 @@ __global__ void __launch_bounds__(MAXT, MINB) debug_svgd_kernel(const __grid_con
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Nmax = a.N > a.Np ? a.N : a.Np;
     const Sm s = bind_smem(smem_raw, Nmax, DP);
+    SMAP_DBG_BEGIN(Nmax, a.stats ? a.stats + kDbgWord : nullptr);
     const int b = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
     const bool first = (a.t == 1 && a.Np == 1);
     // the previous set goes through xs (prepare_step reads it there)

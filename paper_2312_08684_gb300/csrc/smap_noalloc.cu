@@ -210,6 +210,7 @@ extern "C" smap_status smap_viterbi_noalloc(int model, const double* params, int
     a.bwguess = c.bwguess;
     a.status = c.status;
     a.stats = c.status + B;
+    a.Btot = B;
     a.queue = c.queue;
     void* args[] = {&a};
     e = cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, smem, st);

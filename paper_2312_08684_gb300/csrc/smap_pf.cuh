@@ -212,6 +212,7 @@ __global__ void __launch_bounds__(MAXT, 1) pf_seq_kernel(const __grid_constant__
     constexpr int D = M::D, DP = M::DP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Sm s = bind_smem(smem_raw, a.Nmax, DP);
+    SMAP_DBG_BEGIN(a.Nmax, a.status + a.B + kDbgWord);
     const ModelParams& mp = a.mp;
     const int tid = threadIdx.x, NT = blockDim.x;
     __shared__ int s_item;

@@ -4,7 +4,9 @@ transition terms evaluated on the FP32 pipe as pairs of FP32 numbers, about
 inputs are float64 values; the device splits each into an FP32 pair, which
 carries all but the last ~5 of its 53 bits, so the comparison is against the
 function of that pair: relative 2^-44 for exp and sqrt, absolute 2^-45
-(times max(1, |log x|)) for log."""
+(times max(1, |log x|)) for log. exp is held on |x| < 60: further out the
+low FP32 part of the result leaves the normal range (the recursion uses
+exp on [-45, 0])."""
 import numpy as np
 import pytest
 
@@ -30,7 +32,7 @@ def _pair(x):
 
 def test_exp():
     rng = np.random.default_rng(1)
-    x = np.concatenate([rng.uniform(-45.0, 0.0, 20000), rng.uniform(-80.0, 80.0, 5000),
+    x = np.concatenate([rng.uniform(-45.0, 0.0, 20000), rng.uniform(-60.0, 60.0, 5000),
                         [0.0, -1e-12, 1e-12, -0.3465735902799727, 0.3465735902799727, -45.0]])
     got = abi.smap_debug_df(0, x)
     ref = np.exp(_pair(x))
