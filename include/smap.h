@@ -413,6 +413,14 @@ smap_status smap_debug_median_stats(smap_handle* h, int* counts);
  * re-records the batched run's graph at its next call. */
 smap_status smap_debug_record_learned_init(smap_handle* h, float* xinit_all);
 
+/* Counters of the forward recursion (Eq. forward_recursion) over the step
+ * launches since the last call (host [3]; reading resets them): counts[0]
+ * particle-steps scored, counts[1] of those whose best predecessor the FP32
+ * screen could not prove unique (a near-tie: every candidate within the
+ * screen's rounding bound is scored exactly), counts[2] exact candidate
+ * scores computed. Synchronises the stream. */
+smap_status smap_debug_recursion_stats(smap_handle* h, unsigned long long* counts);
+
 /* Kernel launches the library has issued since load (its own kernels only). */
 uint64_t smap_kernel_launches(void);
 

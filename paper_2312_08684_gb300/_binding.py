@@ -38,6 +38,7 @@ EXPORTS = [
     "smap_proposal_loss_grad", "smap_proposal_train", "smap_proposal_last_error", "smap_proposal_capture",
     "smap_set_proposal", "smap_pf_run_batch", "smap_debug_proposal_forward", "smap_debug_record_learned_init",
     "smap_state_size", "smap_save", "smap_load", "smap_debug_df", "smap_debug_bounds_probe",
+    "smap_debug_recursion_stats",
 ]
 MLP_IN_P, MLP_OUT_P, MLP_H = 32, 16, 256
 
@@ -121,6 +122,7 @@ def load():
     L.smap_debug_record_learned_init.argtypes = [_VP, _VP]
     L.smap_state_size.argtypes = [_VP, ctypes.POINTER(ctypes.c_size_t)]
     L.smap_debug_df.argtypes = [_I, _VP, _I, _VP]
+    L.smap_debug_recursion_stats.argtypes = [_VP, _VP]
     L.smap_debug_bounds_probe.argtypes = [_I, _I, _VP, _VP, _VP]
     L.smap_save.argtypes = [_VP, _VP, ctypes.c_size_t]
     L.smap_load.argtypes = [_VP, _VP, ctypes.c_size_t]
@@ -364,6 +366,13 @@ def smap_debug_bounds_probe(rows, index):
     _check(load().smap_debug_bounds_probe(int(rows), int(index), ctypes.c_void_p(v.ctypes.data),
                                           ctypes.c_void_p(c.ctypes.data), ctypes.c_void_p(c[1:].ctypes.data)))
     return float(v[0]), int(c[0]), int(c[1])
+
+
+def smap_debug_recursion_stats(h):
+    """(particle-steps, near-ties, exact candidate scores) since the last read; reading resets them."""
+    out = np.zeros(3, np.uint64)
+    _check(load().smap_debug_recursion_stats(h, ctypes.c_void_p(out.ctypes.data)), h)
+    return tuple(int(v) for v in out)
 
 
 def smap_debug_df(fn, x):

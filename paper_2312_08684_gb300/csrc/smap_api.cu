@@ -315,6 +315,7 @@ struct smap_handle {
     float* ystep = nullptr;    // [B][dy]
     uint8_t* active = nullptr; // [B]
     int* idxbuf = nullptr;     // [B][maxT]
+    unsigned long long* rstats = nullptr;   // [3] recursion counters since the last read
     float* path = nullptr;     // [B][maxT+1][d]
     double* J = nullptr;       // [B]
     // host mirrors
@@ -450,6 +451,7 @@ smap_status launch_seq(smap_handle* h, int v, int items, int mode, const float* 
     a.skip_done = opts.skip_done;
     a.seq_base = opts.seq_base;
     a.Btot = h->B;
+    a.rstats = h->rstats;
     if (opts.L >= 0) a.L = opts.L;
     void* args[] = {&a};
     cudaStream_t ls = opts.stream ? opts.stream : h->stream;
@@ -842,6 +844,17 @@ smap_status smap_debug_median_stats(smap_handle* h, int* counts) {
     return SMAP_OK;
 }
 
+smap_status smap_debug_recursion_stats(smap_handle* h, unsigned long long* counts) {
+    smap_status st = check_usable(h);
+    if (st) return st;
+    if (!counts) return fail(h, SMAP_E_INVAL, "null output");
+    SMAP_CUDA(h, cudaMemcpyAsync(counts, h->rstats, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost,
+                                 h->stream));
+    SMAP_CUDA(h, cudaMemsetAsync(h->rstats, 0, sizeof(unsigned long long) * 4, h->stream));
+    SMAP_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SMAP_OK;
+}
+
 smap_status smap_last_kernel_ms(smap_handle* h, float* seq_ms, float* batch_ms) {
     smap_status st = check_usable(h);
     if (st) return st;
@@ -877,7 +890,8 @@ void smap_destroy(smap_handle* h) {
     if (h->ystep_h) cudaFreeHost(h->ystep_h);
     if (h->active_h) cudaFreeHost(h->active_h);
     void* bufs[] = {h->hist, h->psi, h->phi, h->tcur, h->Nseq, h->Tend, h->order, h->x0, h->f64,
-                    h->bwguess, h->status, h->queue, h->y, h->ystep, h->active, h->idxbuf, h->path, h->J};
+                    h->bwguess, h->status, h->queue, h->y, h->ystep, h->active, h->idxbuf, h->path, h->J,
+                    h->rstats};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -958,6 +972,7 @@ smap_status smap_create(const smap_config* cfg, smap_handle** out) {
         {(void**)&h->idxbuf, sizeof(int) * B * T},
         {(void**)&h->path, sizeof(float) * B * (T + 1) * d},
         {(void**)&h->J, sizeof(double) * B},
+        {(void**)&h->rstats, sizeof(unsigned long long) * 4},
     };
     // fault injection for tests: SMAP_FAIL_ALLOC=k makes the k-th device
     // allocation of this call fail as if the device were out of memory
@@ -973,6 +988,8 @@ smap_status smap_create(const smap_config* cfg, smap_handle** out) {
             return bail(SMAP_E_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
         }
     }
+    e = cudaMemset(h->rstats, 0, sizeof(unsigned long long) * 4);
+    if (e != cudaSuccess) return bail(SMAP_E_CUDA, cudaGetErrorString(e));
     if (cudaMallocHost(&h->ystep_h, sizeof(float) * B * dy) != cudaSuccess ||
         cudaMallocHost(&h->active_h, B) != cudaSuccess) {
         cudaGetLastError();

@@ -65,6 +65,7 @@ struct SeqArgs {
     int skip_done;            // mode 1: skip sequences with tcur >= Tend
     int seq_base;             // without `order`, item k is sequence seq_base + k
     int Btot;                 // sequences of the handle's arrays (debug build's bounds checks)
+    unsigned long long* rstats;  // [3] recursion counters: particle-steps, near-ties, FP64 candidate scores (or null)
     int kernel;               // Stein kernel: 0 RBF, 1 IMQ, 2 Matern 3/2
 };
 

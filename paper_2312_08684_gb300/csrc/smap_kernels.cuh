@@ -1087,7 +1087,8 @@ __device__ __forceinline__ double trans_m64(const ModelParams& mp, const float* 
 // ---------------------------------------------------------------------------
 template <class M, int PPT>
 __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, const double* f64,
-                             const float* xprev, int* best, double* phinew) {
+                             const float* xprev, int* best, double* phinew, unsigned* ntie = nullptr,
+                             unsigned* neval = nullptr) {
     constexpr int D = M::D, DP = M::DP;
     const int tid = threadIdx.x, NT = blockDim.x;
     constexpr float u = 5.9604644775390625e-08f;   // 2^-24
@@ -1199,8 +1200,10 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
             blt[p] = logtrans(row[p], j);
             bs[p] = s.phis[j] + blt[p];
             best[p] = j;
+            if (neval && tid + p * NT < N) ++*neval;
         } else {
             multi = true;
+            if (ntie && tid + p * NT < N) ++*ntie;
         }
     }
     if (multi) {
@@ -1217,6 +1220,7 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
                 for (int c = 0; c < D; ++c) v = fmaf(xc[p][c], gj[c], v);
                 if (v >= thr[p]) {
                     const double lt = logtrans(row[p], j);
+                    if (neval && tid + p * NT < N) ++*neval;
                     const double sv = s.phis[j] + lt;
                     if (sv > bs[p]) { bs[p] = sv; blt[p] = lt; best[p] = j; }
                 }
@@ -1278,6 +1282,8 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
     __shared__ int s_item;
     double* f64 = a.f64 + (size_t)blockIdx.x * a.Nmax * D;
     const float q_extra = init_spread(mp);
+    unsigned n_tie = 0, n_eval = 0;   // this thread's near-tie particles and candidate scores
+    unsigned long long n_ps = 0;      // particle-steps of the block (thread 0)
     for (;;) {
         __syncthreads();
         if (tid == 0) s_item = atomicAdd(a.queue, 1);
@@ -1330,7 +1336,8 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
             double phinew[PPT];
             if (!SMAP_DBG(t >= 1 && t <= a.maxT, kDbgStep, t)) break;
             const float* xprev = (t >= 2) ? a.hist + (((size_t)b * a.maxT + (t - 2)) * a.Nmax) * D : nullptr;
-            viterbi_step<M, PPT>(mp, s, N, Np, f64, xprev, best, phinew);
+            viterbi_step<M, PPT>(mp, s, N, Np, f64, xprev, best, phinew, &n_tie, &n_eval);
+            if (tid == 0) n_ps += (unsigned long long)N;
             __syncthreads();   // all reads of phis / xs done
             bool bad = false;
             float* dst = a.hist + (((size_t)b * a.maxT + (t - 1)) * a.Nmax) * D;
@@ -1365,6 +1372,18 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
             a.tcur[b] = tdone;
             a.bwguess[b] = st.have ? st.med : 0.0f;
         }
+    }
+    if (a.rstats) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            n_tie += __shfl_xor_sync(0xffffffffu, n_tie, o);
+            n_eval += __shfl_xor_sync(0xffffffffu, n_eval, o);
+        }
+        if ((tid & 31) == 0) {
+            if (n_tie) atomicAdd(&a.rstats[1], (unsigned long long)n_tie);
+            if (n_eval) atomicAdd(&a.rstats[2], (unsigned long long)n_eval);
+        }
+        if (tid == 0 && n_ps) atomicAdd(&a.rstats[0], n_ps);
     }
 }
 
