@@ -514,7 +514,7 @@ __device__ float median_sqdist(const Sm& s, int N, float s2, float q_extra, MedS
 template <class M, int PPT>
 __device__ void prepare_step(const ModelParams& mp, const Sm& s, int t, int N, int Np, bool first,
                              const double* x0, const float* yt, double* f64, int prior,
-                             uint64_t seed, uint32_t seq, const float* xinit) {
+                             uint64_t seed, uint32_t seq, const float* xinit, bool df_means = false) {
     constexpr int D = M::D, DP = M::DP;
     const int tid = threadIdx.x, NT = blockDim.x;
     for (int c = tid; c < mp.dy; c += NT) s.zs[c] = yt[c];
@@ -535,6 +535,26 @@ __device__ void prepare_step(const ModelParams& mp, const Sm& s, int t, int N, i
     for (int p = 0; p < PPT; ++p) {
         const int i = tid + p * NT;
         double fd[D];
+        if constexpr (M::kTransDF) {
+            // the recursion alone on given sets: the recursion's double-float
+            // terms read the previous set itself, so only the centred FP32
+            // means of its screen are needed (no FP64 means)
+            if (df_means && i < Np) {
+                float xp[D], fc[D], fr[D];
+                load_row<D, DP>(s.xs, i, xp);
+                M::centred_mean(mp, xp, cf, fc);
+#pragma unroll
+                for (int c = 0; c < D; ++c) fr[c] = __fmul_rn(fc[c], mp.sqrt_qinv_f[c] * kKm);
+                store_row<D, DP>(s.fs, i, fr);
+                if (i < N) {
+                    float xi[D];
+#pragma unroll
+                    for (int c = 0; c < D; ++c) xi[c] = xinit[(size_t)i * D + c];
+                    store_row<D, DP>(s.xs, i, xi);
+                }
+                continue;
+            }
+        }
         if (i < Np) {
             if (first) {
 #pragma unroll
@@ -1064,14 +1084,17 @@ __device__ __forceinline__ double trans_m64(const ModelParams& mp, const float* 
 //   S_ij = A_j + X_i . Y_j,   A_j = phi_{t-1}(j) - max_k phi_{t-1}(k) - |Y_j|^2 / 2,
 // so one pair costs d FMAs of x~ = kKm X against g = kLam f~ = Y / kKm (x~ . g
 // = X . Y, as kKm^2 kLam = 1) plus the running top two. Rounding (u = 2^-24,
-// first order): x~ carries 4u relative error per coordinate, g 3u, and the
-// FP32 constants kKm^2 kLam differ from 1 by 1.5u, so x~ . g is within
-// 7.5u |X_i| |Y_j| of X . Y; A_j in FP32 from the FP32 phi~ and f~ is within
-// (d + 6.5) u H_j of the exact value, H_j = |phi~_j| + kLam |f~_j|^2 / 2; the
-// start value aU_j = A_j + e_j adds u (H_j + e_j); the FMA chain adds
-// d u (|aU_j| + |x~_i| |g_j|). With e_j = (2d + 8) u H_j (1.01) plus a margin
-// for the FP64 evaluation's own rounding, and E_i = (d + 8) u |x~_i| max_j |g_j|
-// (1.01) (plus the same margin), the computed chain v_ij satisfies
+// first order): the FP32 scale qk = sqrt(Q^-1) kKm carries 2.5u, x~ and f~
+// each two roundings (f~ is rounded from FP64, or from the double-float
+// centred mean of the recursion-only path), g one more, and kKm^2 kLam differs
+// from 1 by 1.5u, so x~ . g is within 11.5u |X_i| |Y_j| of X . Y; A_j in FP32
+// from the FP32 phi~ and f~ is within (d + 12.5) u H_j of the exact value,
+// H_j = |phi~_j| + kLam |f~_j|^2 / 2; the start value aU_j = A_j + e_j adds
+// u (H_j + e_j); the FMA chain adds d u (|aU_j| + |x~_i| |g_j|). With
+// e_j = (2d + 14) u H_j (1.01) plus a margin for the rounding of the exact
+// evaluation (2^-46 of the magnitudes involved), and
+// E_i = (d + 12) u |x~_i| max_j |g_j| (1.01) (plus the same margin), the
+// computed chain v_ij satisfies
 //   v_ij - 2 e_j - E_i <= S_ij <= v_ij + E_i.
 // So with v1 = max_j v_ij at j1 (first j attaining it) and v2 the largest v_ij
 // of every other j, v1 - v2 > 2 e_j1 + 2 E_i proves j1 the unique maximum of
@@ -1092,12 +1115,14 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
     constexpr int D = M::D, DP = M::DP;
     const int tid = threadIdx.x, NT = blockDim.x;
     constexpr float u = 5.9604644775390625e-08f;   // 2^-24
-    constexpr float Ke = (2 * D + 8) * u * 1.01f;   // e_j per unit of H_j
-    constexpr float Ki = (D + 8) * u * 1.01f;       // E_i per unit of |x~_i| max |g|
-    constexpr double K64 = 1.4210854715202004e-14;  // 2^-46: margin of the FP64 scores
+    constexpr float Ke = (2 * D + 14) * u * 1.01f;  // e_j per unit of H_j
+    constexpr float Ki = (D + 12) * u * 1.01f;      // E_i per unit of |x~_i| max |g|
+    constexpr float K64 = 1.4210854715202004e-14f;  // 2^-46: margin of the exact scores
     double pmax = -INFINITY;
     for (int j = tid; j < Np; j += NT) pmax = fmax(pmax, s.phis[j]);
     pmax = block_max_d(pmax, s.redd);
+    // FP32 magnitudes for the margin of the exact scores: |phi_j| <= |phi~_j| + |max|
+    const float mag0 = 2.0f * fabsf((float)pmax) + fabsf(mp.ltc[0]);
     float2* ab = reinterpret_cast<float2*>(s.gs);   // (aU_j, 2 e_j)
     float gmax2 = 0.0f;
     for (int j = tid; j < Np; j += NT) {
@@ -1116,8 +1141,7 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
         gmax2 = fmaxf(gmax2, G);
         const float half = 0.5f * kLam * F;
         const float H = fabsf(ph) + half;
-        const float e = Ke * H + (float)(K64 * (fabs(s.phis[j]) + fabs(pmax) + fabs(mp.logtrans_c) +
-                                                (double)(kLam * F)));
+        const float e = Ke * H + K64 * (fabsf(ph) + mag0 + kLam * F);
         ab[j] = make_float2((ph - half) + e, 2.0f * e);
     }
     const float gmax = sqrtf(block_max_f(gmax2, s.redf)) * 1.0000005f;
@@ -1139,10 +1163,14 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
             xc[p][c] = (xr[c] - cf[c]) * qk[c];
             X = fmaf(xc[p][c], xc[p][c], X);
         }
-        Ei[p] = Ki * sqrtf(X) * 1.0000005f * gmax + (float)(K64 * (double)(kLam * X));
+        Ei[p] = Ki * sqrtf(X) * 1.0000005f * gmax + K64 * kLam * X;
     }
-    // One FP32 pass: per particle the largest chain value v1 (first j
-    // attaining it) and the largest value v2 of every other j.
+    // One FP32 pass: per particle the largest chain value v1 and the largest
+    // value v2 of every other j (three min/max per pair), and the chunk of 32
+    // predecessors in which v1 was first reached; the chunk is then scanned
+    // again for the first j whose chain value (computed the same way, so
+    // bit-identical) equals v1.
+    constexpr int kChunk = 32;
     float v1[PPT], v2[PPT];
     int j1[PPT];
 #pragma unroll
@@ -1151,20 +1179,41 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
         v2[p] = -INFINITY;
         j1[p] = 0;
     }
-    for (int j = 0; j < Np; ++j) {
-        float gj[D];
-        load_row<D, DP>(s.fs, j, gj);
-        const float aU = ab[j].x;
+    for (int j0 = 0; j0 < Np; j0 += kChunk) {
+        float vb[PPT];
 #pragma unroll
-        for (int p = 0; p < PPT; ++p) {
-            float v = aU;
+        for (int p = 0; p < PPT; ++p) vb[p] = v1[p];
+        const int je = min(j0 + kChunk, Np);
+        for (int j = j0; j < je; ++j) {
+            float gj[D];
+            load_row<D, DP>(s.fs, j, gj);
+            const float aU = ab[j].x;
+#pragma unroll
+            for (int p = 0; p < PPT; ++p) {
+                float v = aU;
+#pragma unroll
+                for (int c = 0; c < D; ++c) v = fmaf(xc[p][c], gj[c], v);
+                const float lo = fminf(v1[p], v);
+                v1[p] = fmaxf(v1[p], v);
+                v2[p] = fmaxf(v2[p], lo);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) j1[p] = v1[p] > vb[p] ? j0 : j1[p];
+    }
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        const int j0 = j1[p], je = min(j0 + kChunk, Np);
+        for (int j = j0; j < je; ++j) {
+            float gj[D];
+            load_row<D, DP>(s.fs, j, gj);
+            float v = ab[j].x;
 #pragma unroll
             for (int c = 0; c < D; ++c) v = fmaf(xc[p][c], gj[c], v);
-            const bool nb = v > v1[p];
-            j1[p] = nb ? j : j1[p];
-            const float lo = fminf(v1[p], v);
-            v1[p] = fmaxf(v1[p], v);
-            v2[p] = fmaxf(v2[p], lo);
+            if (v == v1[p]) {
+                j1[p] = j;
+                break;
+            }
         }
     }
     // candidate threshold: v_ij >= v1 - 2 e_j1 - 2 E_i can still be the maximum
@@ -1206,23 +1255,48 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
             if (ntie && tid + p * NT < N) ++*ntie;
         }
     }
-    if (multi) {
-        // near-ties (rare): every candidate j in FP64, lowest j first
-        for (int j = 0; j < Np; ++j) {
-            float gj[D];
-            load_row<D, DP>(s.fs, j, gj);
-            const float aU = ab[j].x;
+    if (__any_sync(0xffffffffu, multi)) {
+        // near-ties (rare): the warp takes each such particle in turn, its 32
+        // lanes splitting the predecessors; every candidate is scored exactly
+        // and the warp keeps the largest score (lowest j on ties)
+        const int lane = tid & 31;
 #pragma unroll
-            for (int p = 0; p < PPT; ++p) {
-                if (uniq[p]) continue;
-                float v = aU;
+        for (int p = 0; p < PPT; ++p) {
+            unsigned m = __ballot_sync(0xffffffffu, !uniq[p] && tid + p * NT < N);
+            while (m) {
+                const int L = __ffs(m) - 1;
+                m &= m - 1;
+                float xb[D];
 #pragma unroll
-                for (int c = 0; c < D; ++c) v = fmaf(xc[p][c], gj[c], v);
-                if (v >= thr[p]) {
-                    const double lt = logtrans(row[p], j);
-                    if (neval && tid + p * NT < N) ++*neval;
-                    const double sv = s.phis[j] + lt;
-                    if (sv > bs[p]) { bs[p] = sv; blt[p] = lt; best[p] = j; }
+                for (int c = 0; c < D; ++c) xb[c] = __shfl_sync(0xffffffffu, xc[p][c], L);
+                const float tb = __shfl_sync(0xffffffffu, thr[p], L);
+                const int rb = __shfl_sync(0xffffffffu, row[p], L);
+                double bsv = -INFINITY, blv = 0.0;
+                int bj = 0x7fffffff;
+                for (int j = lane; j < Np; j += 32) {
+                    float gj[D];
+                    load_row<D, DP>(s.fs, j, gj);
+                    float v = ab[j].x;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) v = fmaf(xb[c], gj[c], v);
+                    if (v >= tb) {
+                        const double lt = logtrans(rb, j);
+                        if (neval) ++*neval;
+                        const double sv = s.phis[j] + lt;
+                        if (sv > bsv) { bsv = sv; blv = lt; bj = j; }
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    const double osv = __shfl_xor_sync(0xffffffffu, bsv, o);
+                    const double olv = __shfl_xor_sync(0xffffffffu, blv, o);
+                    const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+                    if (osv > bsv || (osv == bsv && oj < bj)) { bsv = osv; blv = olv; bj = oj; }
+                }
+                if (lane == L && bsv > -INFINITY) {
+                    bs[p] = bsv;
+                    blt[p] = blv;
+                    best[p] = bj;
                 }
             }
         }
@@ -1326,7 +1400,7 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
                                    ? a.hist + (((size_t)b * a.maxT + (t - 1)) * a.Nmax) * D
                                    : (a.xinit ? a.xinit + (size_t)b * a.Nmax * D : nullptr);
             prepare_step<M, PPT>(mp, s, t, N, Np, t == 1, a.x0 + (size_t)b * D, yt, f64, a.prior,
-                                 a.seed, (uint32_t)b, xin);
+                                 a.seed, (uint32_t)b, xin, a.viterbi_only && t >= 2);
             if (!a.viterbi_only) {
                 st.fresh = 1;
                 svgd_iterations<M, PPT, TPP>(mp, s, N, Np, a.L, a.eps, a.bw_rule, a.bw_value, a.prior, st,

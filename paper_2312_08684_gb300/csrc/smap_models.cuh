@@ -11,6 +11,7 @@
 // arithmetic (about 48 bits, on the FP32 pipe) from the FP32 particles:
 //   trans_sq_df(mp, x, xp)          |x - f_t(xp)|^2_{Q^-1}, the residual formed
 //                                   from x and the previous particle xp
+//   centred_mean(mp, xp, c, out)    f_t(xp) - c rounded once to FP32
 //   loglik_df(mp, z, x)             log p(z | x)
 // Parameter layouts are documented in include/smap.h; aux[] holds constants
 // the host precomputes in FP64 (listed per model; aux[4] = -1/(2 r) for the
@@ -88,6 +89,14 @@ struct CVTransition {
         f[2] = x[2];
         f[3] = x[3];
     }
+    // f_t(xp) - c, rounded once from its double-float value
+    __device__ static void centred_mean(const ModelParams& mp, const float* xp, const float* cf, float* out) {
+        const df::F dt = dfp(mp, 0);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) out[c] = df::add(df_diff(xp[c], cf[c]), df::mul_f(dt, xp[c + 2])).hi;
+#pragma unroll
+        for (int c = 2; c < 4; ++c) out[c] = __fsub_rn(xp[c], cf[c]);
+    }
     // position residual (x - xp) - dt vp, velocity residual v - vp
     __device__ static df::F trans_sq_df(const ModelParams& mp, const float* x, const float* xp) {
         const df::F dt = dfp(mp, 0);
@@ -110,6 +119,10 @@ struct CVTransition {
 struct ModelRangeZV {
     static constexpr int KIND = 6, D = 2, DP = 2, DY = 8;
     static constexpr bool kTransDF = true, kLikDF = true;
+    __device__ static void centred_mean(const ModelParams&, const float* xp, const float* cf, float* out) {
+        out[0] = __fsub_rn(xp[0], cf[0]);
+        out[1] = __fsub_rn(xp[1], cf[1]);
+    }
     __device__ static df::F trans_sq_df(const ModelParams& mp, const float* x, const float* xp) {
         return df::add(df::mul(df::sqr(df_diff(x[0], xp[0])), dfqinv(mp, 0)),
                        df::mul(df::sqr(df_diff(x[1], xp[1])), dfqinv(mp, 1)));
@@ -377,6 +390,14 @@ template <int NL>
 struct ModelPlanarArm {
     static constexpr int KIND = 4, D = 2 * NL, DP = (2 * NL + 3) & ~3, DY = 2;
     static constexpr bool kTransDF = true, kLikDF = false;
+    __device__ static void centred_mean(const ModelParams& mp, const float* xp, const float* cf, float* out) {
+        const df::F dt = dfp(mp, 0);
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            out[k] = df::add(df_diff(xp[k], cf[k]), df::mul_f(dt, xp[NL + k])).hi;
+            out[NL + k] = __fsub_rn(xp[NL + k], cf[NL + k]);
+        }
+    }
     // angle residual (th - thp) - dt wp, rate residual w - wp
     __device__ static df::F trans_sq_df(const ModelParams& mp, const float* x, const float* xp) {
         const df::F dt = dfp(mp, 0);
