@@ -458,6 +458,7 @@ def main():
     hist_dev = torch.empty((wl.B, wl.maxT, wl.N, wl.d), dtype=torch.float32, device=dev)
     abi.smap_get_history(est.h, hist_dev)
     abi.smap_viterbi(est.h, hist_dev, y_dev, T_seq, None, path_dev, J_dev)
+    abi.smap_debug_recursion_stats(est.h)          # counters from here on: the timed recursion runs
     vit_ms = []
     for _ in range(3):
         flush.zero_()
@@ -469,6 +470,7 @@ def main():
         ev1.synchronize()
         vit_ms.append(ev0.elapsed_time(ev1))
     vit_ms = max_over_ranks(float(np.mean(vit_ms)), dist, dev)
+    n_ps, n_tie, n_eval = abi.smap_debug_recursion_stats(est.h)
     del hist_dev
     est.close()
     del y_dev, path_dev, J_dev, flush
@@ -507,7 +509,9 @@ def main():
                 "d2h_bytes_per_step": int(path_pin.numel() * 4 + J_pin.numel() * 8)},
         "viterbi": {"what": "smap_viterbi alone on the same particle sets (history copy, recursion, "
                             "backtrack)", "ms": vit_ms, "achieved": vit_ach, "peak": peak, "unit": "Gop/s",
-                    "frac": vit_ach / peak, "ops_per_pair": 2 * wl.d + 2},
+                    "frac": vit_ach / peak, "ops_per_pair": 2 * wl.d + 2,
+                    "near_tie_fraction": n_tie / max(n_ps, 1),
+                    "exact_scores_per_particle_step": n_eval / max(n_ps, 1)},
         "gpu_launches": int(launches),
         "clocks": clk,
     }

@@ -83,4 +83,4 @@ def build(verbose: bool = False, jobs: int | None = None, debug: bool = False) -
 
 
 if __name__ == "__main__":
-    print(build(verbose=True))
+    print(build(verbose=True, debug="--debug" in sys.argv[1:]))

@@ -850,6 +850,8 @@ smap_status smap_debug_recursion_stats(smap_handle* h, unsigned long long* count
     if (!counts) return fail(h, SMAP_E_INVAL, "null output");
     SMAP_CUDA(h, cudaMemcpyAsync(counts, h->rstats, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost,
                                  h->stream));
+    SMAP_CUDA(h, cudaStreamSynchronize(h->stream));
+    counts[2] += counts[0] - counts[1];   // one exact score per particle proven unique, plus the near-ties' candidates
     SMAP_CUDA(h, cudaMemsetAsync(h->rstats, 0, sizeof(unsigned long long) * 4, h->stream));
     SMAP_CUDA(h, cudaStreamSynchronize(h->stream));
     return SMAP_OK;

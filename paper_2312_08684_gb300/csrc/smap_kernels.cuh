@@ -1110,8 +1110,8 @@ __device__ __forceinline__ double trans_m64(const ModelParams& mp, const float* 
 // ---------------------------------------------------------------------------
 template <class M, int PPT>
 __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, const double* f64,
-                             const float* xprev, int* best, double* phinew, unsigned* ntie = nullptr,
-                             unsigned* neval = nullptr) {
+                             const float* xprev, int* best, double* phinew,
+                             unsigned long long* rcnt = nullptr) {
     constexpr int D = M::D, DP = M::DP;
     const int tid = threadIdx.x, NT = blockDim.x;
     constexpr float u = 5.9604644775390625e-08f;   // 2^-24
@@ -1249,10 +1249,9 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
             blt[p] = logtrans(row[p], j);
             bs[p] = s.phis[j] + blt[p];
             best[p] = j;
-            if (neval && tid + p * NT < N) ++*neval;
         } else {
             multi = true;
-            if (ntie && tid + p * NT < N) ++*ntie;
+            if (rcnt && tid + p * NT < N) atomicAdd(&rcnt[1], 1ull);
         }
     }
     if (__any_sync(0xffffffffu, multi)) {
@@ -1281,7 +1280,7 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
                     for (int c = 0; c < D; ++c) v = fmaf(xb[c], gj[c], v);
                     if (v >= tb) {
                         const double lt = logtrans(rb, j);
-                        if (neval) ++*neval;
+                        if (rcnt) atomicAdd(&rcnt[2], 1ull);
                         const double sv = s.phis[j] + lt;
                         if (sv > bsv) { bsv = sv; blv = lt; bj = j; }
                     }
@@ -1333,6 +1332,7 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
         }
         phinew[p] = ll + blt[p] + s.phis[best[p]];
     }
+    if (rcnt && tid == 0) rcnt[0] += (unsigned long long)N;
 }
 
 // Extra squared-distance spread the initial noise adds: 2 sum_d q_d.
@@ -1356,8 +1356,11 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
     __shared__ int s_item;
     double* f64 = a.f64 + (size_t)blockIdx.x * a.Nmax * D;
     const float q_extra = init_spread(mp);
-    unsigned n_tie = 0, n_eval = 0;   // this thread's near-tie particles and candidate scores
-    unsigned long long n_ps = 0;      // particle-steps of the block (thread 0)
+    // recursion counters of the block (shared, so that nothing stays live in
+    // registers across the persistent loop): particle-steps, near-ties,
+    // exact scores beyond one per particle
+    __shared__ unsigned long long s_rcnt[3];
+    if (tid < 3) s_rcnt[tid] = 0ull;
     for (;;) {
         __syncthreads();
         if (tid == 0) s_item = atomicAdd(a.queue, 1);
@@ -1410,8 +1413,7 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
             double phinew[PPT];
             if (!SMAP_DBG(t >= 1 && t <= a.maxT, kDbgStep, t)) break;
             const float* xprev = (t >= 2) ? a.hist + (((size_t)b * a.maxT + (t - 2)) * a.Nmax) * D : nullptr;
-            viterbi_step<M, PPT>(mp, s, N, Np, f64, xprev, best, phinew, &n_tie, &n_eval);
-            if (tid == 0) n_ps += (unsigned long long)N;
+            viterbi_step<M, PPT>(mp, s, N, Np, f64, xprev, best, phinew, s_rcnt);
             __syncthreads();   // all reads of phis / xs done
             bool bad = false;
             float* dst = a.hist + (((size_t)b * a.maxT + (t - 1)) * a.Nmax) * D;
@@ -1447,18 +1449,8 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
             a.bwguess[b] = st.have ? st.med : 0.0f;
         }
     }
-    if (a.rstats) {
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            n_tie += __shfl_xor_sync(0xffffffffu, n_tie, o);
-            n_eval += __shfl_xor_sync(0xffffffffu, n_eval, o);
-        }
-        if ((tid & 31) == 0) {
-            if (n_tie) atomicAdd(&a.rstats[1], (unsigned long long)n_tie);
-            if (n_eval) atomicAdd(&a.rstats[2], (unsigned long long)n_eval);
-        }
-        if (tid == 0 && n_ps) atomicAdd(&a.rstats[0], n_ps);
-    }
+    __syncthreads();
+    if (a.rstats && tid < 3 && s_rcnt[tid]) atomicAdd(&a.rstats[tid], s_rcnt[tid]);
 }
 
 // Debug: n iterations of SVGD from given particles (one CTA per sequence).
