@@ -1,6 +1,6 @@
 """The forward recursion alone (smap_viterbi) on particle sets from a real run.
 
-  python -m measure.recursion [--config C2|C3|C4] [--B 1024] [--reps 3]
+  python -m measure.recursion [--config C2|C3|C4] [--B 1024] [--reps 3] [--variant V]
 
 Runs the configuration's batched method once (the particle sets SVGD
 produces), then times smap_viterbi on those sets with CUDA events on the
@@ -32,6 +32,7 @@ def main(argv=None):
     ap.add_argument("--config", default="C3", choices=["C2", "C3", "C4"])
     ap.add_argument("--B", type=int, default=1024)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--variant", type=int, default=None, help="launch shape of the recursion (smap_set_variant)")
     args = ap.parse_args(argv)
     import torch
     wl = bench.make_workload(args.config, 0, args.B)
@@ -46,6 +47,8 @@ def main(argv=None):
         hist = torch.empty((wl.B, wl.maxT, wl.N, wl.d), dtype=torch.float32, device="cuda")
         abi.smap_get_history(est.h, hist)
         abi.smap_debug_recursion_stats(est.h)
+        if args.variant is not None:
+            est.set_variant(args.variant)
         ms = []
         for _ in range(args.reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -62,7 +65,8 @@ def main(argv=None):
     peak = bench.alu_peak_gops(pk.get("sm_max_mhz", 2070.0), sms)
     ops = bench.recursion_ops(wl)
     best = min(ms)
-    print(json.dumps({"config": args.config, "B": wl.B, "N": wl.N, "d": wl.d, "batch_kernel_ms": batch_ms,
+    print(json.dumps({"config": args.config, "B": wl.B, "N": wl.N, "d": wl.d, "variant": args.variant,
+                      "batch_kernel_ms": batch_ms,
                       "viterbi_ms": ms, "achieved_gops": ops / (best / 1e3) / 1e9, "peak_gops": peak,
                       "frac": ops / (best / 1e3) / 1e9 / peak, "particle_steps": n_ps,
                       "near_tie_fraction": n_tie / max(n_ps, 1),

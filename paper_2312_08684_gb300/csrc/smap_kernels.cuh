@@ -41,8 +41,11 @@ __host__ __device__ inline SmemLayout smem_layout(int Nmax, int DP) {
     size_t off = 0;
     L.phis = off; off = align16(off + sizeof(double) * Nmax);
     L.xs = off;   off = align16(off + sizeof(float) * Nmax * DP);
-    L.gs = off;   off = align16(off + sizeof(float) * Nmax * (DP < 2 ? 2 : DP));
-    L.fs = off;   off = align16(off + sizeof(float) * Nmax * DP);
+    // gs: SVGD's w rows, or the recursion's aU and 2e arrays (2 Nmax + 4)
+    const size_t gsf = (size_t)Nmax * (DP < 2 ? 2 : DP);
+    L.gs = off;   off = align16(off + sizeof(float) * (gsf > 2 * (size_t)Nmax + 4 ? gsf : 2 * (size_t)Nmax + 4));
+    // fs: one spare row (the recursion pads an odd predecessor count to a pair)
+    L.fs = off;   off = align16(off + sizeof(float) * (Nmax + 1) * DP);
     L.nrm = off;  off = align16(off + sizeof(float) * Nmax);
     L.phf = off;  off = align16(off + sizeof(float) * Nmax);
     L.cand = off; off = align16(off + sizeof(uint32_t) * kCandCap);
@@ -1073,6 +1076,23 @@ __device__ __forceinline__ double trans_m64(const ModelParams& mp, const float* 
     return m64;
 }
 
+// Two FP32 lanes in one 64-bit register: the packed FMA (fma.rn.f32x2) rounds
+// each lane exactly as fmaf does, in one issue slot.
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // a7: forward recursion. The argmax over j of phi_{t-1}(j) + log p(x_i | x^j)
 // is screened in FP32 with a rigorous rounding bound, and every j that can
@@ -1123,9 +1143,18 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
     pmax = block_max_d(pmax, s.redd);
     // FP32 magnitudes for the margin of the exact scores: |phi_j| <= |phi~_j| + |max|
     const float mag0 = 2.0f * fabsf((float)pmax) + fabsf(mp.ltc[0]);
-    float2* ab = reinterpret_cast<float2*>(s.gs);   // (aU_j, 2 e_j)
+    // per predecessor: aU_j (start of the chain) and 2 e_j, in separate arrays;
+    // g_j = kLam f~_j goes into fs as predecessor pairs (2q, 2q+1) interleaved
+    // per coordinate, [q][c][2], after every row has been read
+    const int Npad = (Np + 1) & ~1;
+    float* aUa = s.gs;
+    float* wa = s.gs + Npad;
     float gmax2 = 0.0f;
-    for (int j = tid; j < Np; j += NT) {
+    float gown[PPT][D];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int j = tid + k * NT;
+        if (j >= Np) continue;
         const double dphi = s.phis[j] - pmax;
         const float ph = (float)dphi;
         float fr[D];
@@ -1134,17 +1163,34 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             F = fmaf(fr[c], fr[c], F);
-            fr[c] *= kLam;
-            G = fmaf(fr[c], fr[c], G);
+            gown[k][c] = fr[c] * kLam;
+            G = fmaf(gown[k][c], gown[k][c], G);
         }
-        store_row<D, DP>(s.fs, j, fr);
         gmax2 = fmaxf(gmax2, G);
         const float half = 0.5f * kLam * F;
         const float H = fabsf(ph) + half;
         const float e = Ke * H + K64 * (fabsf(ph) + mag0 + kLam * F);
-        ab[j] = make_float2((ph - half) + e, 2.0f * e);
+        aUa[j] = (ph - half) + e;
+        wa[j] = 2.0f * e;
     }
-    const float gmax = sqrtf(block_max_f(gmax2, s.redf)) * 1.0000005f;
+    const float gmax = sqrtf(block_max_f(gmax2, s.redf)) * 1.0000005f;   // its barriers: every fs row read
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int j = tid + k * NT;
+        if (j >= Np) continue;
+        float* gq = s.fs + (size_t)(j >> 1) * 2 * DP + (j & 1);
+#pragma unroll
+        for (int c = 0; c < D; ++c) gq[2 * c] = gown[k][c];
+    }
+    if (tid == 0 && (Np & 1)) {   // the pad predecessor: never above any other
+        aUa[Np] = -INFINITY;
+        float* gq = s.fs + (size_t)(Np >> 1) * 2 * DP + 1;
+#pragma unroll
+        for (int c = 0; c < D; ++c) gq[2 * c] = 0.0f;
+    }
+    __syncthreads();
+    // g of predecessor j, coordinate c, from the interleaved pairs
+    auto gval = [&](int j, int c) { return s.fs[(size_t)(j >> 1) * 2 * DP + 2 * c + (j & 1)]; };
     float xc[PPT][D], Ei[PPT];
     float cf[D], qk[D];
 #pragma unroll
@@ -1169,47 +1215,57 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
     // value v2 of every other j (three min/max per pair), and the chunk of 32
     // predecessors in which v1 was first reached; the chunk is then scanned
     // again for the first j whose chain value (computed the same way, so
-    // bit-identical) equals v1.
+    // bit-identical) equals v1. The pass takes predecessors in pairs: one
+    // packed FMA advances the chains of j and j + 1 together.
     constexpr int kChunk = 32;
     float v1[PPT], v2[PPT];
     int j1[PPT];
+    unsigned long long xd[PPT][D];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         v1[p] = -INFINITY;
         v2[p] = -INFINITY;
         j1[p] = 0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) xd[p][c] = pk2(xc[p][c], xc[p][c]);
     }
-    for (int j0 = 0; j0 < Np; j0 += kChunk) {
+    const unsigned long long* g2 = reinterpret_cast<const unsigned long long*>(s.fs);
+    const unsigned long long* a2 = reinterpret_cast<const unsigned long long*>(aUa);
+    for (int q0 = 0; q0 < Npad / 2; q0 += kChunk / 2) {
         float vb[PPT];
 #pragma unroll
         for (int p = 0; p < PPT; ++p) vb[p] = v1[p];
-        const int je = min(j0 + kChunk, Np);
-        for (int j = j0; j < je; ++j) {
-            float gj[D];
-            load_row<D, DP>(s.fs, j, gj);
-            const float aU = ab[j].x;
+        const int qe = min(q0 + kChunk / 2, Npad / 2);
+        for (int q = q0; q < qe; ++q) {
+            unsigned long long gp[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) gp[c] = g2[(size_t)q * DP + c];
+            const unsigned long long aU = a2[q];
 #pragma unroll
             for (int p = 0; p < PPT; ++p) {
-                float v = aU;
+                unsigned long long v = aU;
 #pragma unroll
-                for (int c = 0; c < D; ++c) v = fmaf(xc[p][c], gj[c], v);
-                const float lo = fminf(v1[p], v);
-                v1[p] = fmaxf(v1[p], v);
+                for (int c = 0; c < D; ++c) v = ffma2(xd[p][c], gp[c], v);
+                float va, vz;
+                upk2(v, va, vz);
+                float lo = fminf(v1[p], va);
+                v1[p] = fmaxf(v1[p], va);
+                v2[p] = fmaxf(v2[p], lo);
+                lo = fminf(v1[p], vz);
+                v1[p] = fmaxf(v1[p], vz);
                 v2[p] = fmaxf(v2[p], lo);
             }
         }
 #pragma unroll
-        for (int p = 0; p < PPT; ++p) j1[p] = v1[p] > vb[p] ? j0 : j1[p];
+        for (int p = 0; p < PPT; ++p) j1[p] = v1[p] > vb[p] ? 2 * q0 : j1[p];
     }
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         const int j0 = j1[p], je = min(j0 + kChunk, Np);
         for (int j = j0; j < je; ++j) {
-            float gj[D];
-            load_row<D, DP>(s.fs, j, gj);
-            float v = ab[j].x;
+            float v = aUa[j];
 #pragma unroll
-            for (int c = 0; c < D; ++c) v = fmaf(xc[p][c], gj[c], v);
+            for (int c = 0; c < D; ++c) v = fmaf(xc[p][c], gval(j, c), v);
             if (v == v1[p]) {
                 j1[p] = j;
                 break;
@@ -1221,7 +1277,7 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
     bool uniq[PPT];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
-        const float m = (ab[j1[p]].y + 2.0f * Ei[p]) * 1.0000005f;
+        const float m = (wa[j1[p]] + 2.0f * Ei[p]) * 1.0000005f;
         uniq[p] = (v1[p] - v2[p]) > m;
         thr[p] = v1[p] - m;
     }
@@ -1273,11 +1329,9 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
                 double bsv = -INFINITY, blv = 0.0;
                 int bj = 0x7fffffff;
                 for (int j = lane; j < Np; j += 32) {
-                    float gj[D];
-                    load_row<D, DP>(s.fs, j, gj);
-                    float v = ab[j].x;
+                    float v = aUa[j];
 #pragma unroll
-                    for (int c = 0; c < D; ++c) v = fmaf(xb[c], gj[c], v);
+                    for (int c = 0; c < D; ++c) v = fmaf(xb[c], gval(j, c), v);
                     if (v >= tb) {
                         const double lt = logtrans(rb, j);
                         if (rcnt) atomicAdd(&rcnt[2], 1ull);
