@@ -283,6 +283,23 @@ int pick_variant(int d, int Nmax, int B, int sms) {
     return variant_threads(1, Nmax) ? 1 : 2;
 }
 
+// Block size of recursion variant v for Nmax particles, or 0 if it cannot hold them.
+int rec_variant_threads(int v, int Nmax) {
+    const RecVariantInfo& vi = kRecVariants[v];
+    const int nt = std::max(round_up((Nmax + vi.ppt - 1) / vi.ppt, 32), 32);
+    return nt <= vi.maxt ? nt : 0;
+}
+
+// Built-in choice of recursion variant: the first that holds Nmax. Two
+// particles per thread (each predecessor row loaded once for both) with the
+// registers of a 512-thread block measured fastest on the data-association,
+// range-only and arm workloads (N = 512, 256, 1024).
+int pick_rec_variant(int, int Nmax) {
+    for (int v = 0; v < kNumRecVariants; ++v)
+        if (rec_variant_threads(v, Nmax)) return v;
+    return -1;
+}
+
 }  // namespace smap
 
 struct smap_handle {
@@ -324,7 +341,7 @@ struct smap_handle {
     cudaGraphExec_t graph = nullptr;
     int graph_variant = -2, graph_grid = 0, graph_threads = 0, graph_items = -1;
     int last_threads = 0, last_grid = 0;
-    bool configured[kNumVariants * 2] = {};   // shared-memory carveout set
+    bool configured[kNumVariants * 2 + kNumRecVariants] = {};   // shared-memory carveout set
     bool capturing = false;                    // inside smap_run_batch's stream capture
     // pinned staging of smap_step's inputs; step_done marks when they were consumed
     float* ystep_h = nullptr;
@@ -375,8 +392,11 @@ smap_status configure_kernel(smap_handle* h, const void* fn, size_t smem) {
     // (smap_run_batch), and no call of this library ever lowers it
     if (h->capturing) return SMAP_OK;
     SMAP_CUDA(h, ensure_dynamic_smem(fn, smem));
-    for (int k = 0; k < kNumVariants; ++k) {
-        bool* flag = fn == h->K->seq[k] ? &h->configured[k] : fn == h->K->dbg[k] ? &h->configured[kNumVariants + k] : nullptr;
+    for (int k = 0; k < kNumVariants || k < kNumRecVariants; ++k) {
+        bool* flag = k < kNumVariants && fn == h->K->seq[k]      ? &h->configured[k]
+                     : k < kNumVariants && fn == h->K->dbg[k]    ? &h->configured[kNumVariants + k]
+                     : k < kNumRecVariants && fn == h->K->rec[k] ? &h->configured[2 * kNumVariants + k]
+                                                                 : nullptr;
         if (!flag) continue;
         if (!*flag) {
             // the whole unified L1 as shared memory: as many resident sequences as registers allow
@@ -463,6 +483,56 @@ smap_status launch_seq(smap_handle* h, int v, int items, int mode, const float* 
     h->last_grid = grid;
     if (grid_out) *grid_out = grid;
     if (threads_out) *threads_out = nt;
+    return SMAP_OK;
+}
+
+// The recursion alone on the particle sets in h->hist (every sequence from
+// t = 1; the state reset beforehand): rec_kernel over the work queue.
+smap_status launch_rec(smap_handle* h) {
+    const int v = pick_rec_variant(h->d, h->Nmax);
+    const int nt = v >= 0 ? rec_variant_threads(v, h->Nmax) : 0;
+    if (!nt) return fail(h, SMAP_E_UNSUPPORTED, "no recursion kernel variant holds N particles");
+    const void* fn = h->K->rec[v];
+    const size_t smem = rec_smem_layout(h->Nmax, h->K->DP).total;
+    smap_status st = configure_kernel(h, fn, smem);
+    if (st) return st;
+    int occ = 0;
+    SMAP_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nt, smem));
+    if (occ < 1) return fail(h, SMAP_E_UNSUPPORTED, "recursion kernel does not fit on an SM");
+    // the FP64 scratch holds one [Nmax][d] slice per sequence: grid <= B
+    const int grid = std::max(1, std::min(h->B, occ * h->num_sms));
+    SeqArgs a;
+    memset(&a, 0, sizeof(a));
+    a.mp = h->mp;
+    a.B = h->B;
+    a.Nmax = h->Nmax;
+    a.maxT = h->maxT;
+    a.seed = h->cfg.seed;
+    a.y = h->y;
+    a.x0 = h->x0;
+    a.hist = h->hist;
+    a.psi = h->psi;
+    a.phi = h->phi;
+    a.tcur = h->tcur;
+    a.Nseq = h->Nseq;
+    a.Tend = h->Tend;
+    a.order = h->order;
+    a.f64 = h->f64;
+    a.bwguess = h->bwguess;
+    a.status = h->status;
+    a.stats = h->status + h->B;
+    a.queue = h->queue;
+    a.viterbi_only = 1;
+    a.y_full = 1;
+    a.Btot = h->B;
+    a.rstats = h->rstats;
+    void* args[] = {&a};
+    SMAP_CUDA(h, cudaMemsetAsync(a.queue, 0, sizeof(int), h->stream));
+    SMAP_CUDA(h, cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, smem, h->stream));
+    SMAP_CUDA(h, cudaGetLastError());
+    g_launches.fetch_add(1);
+    h->last_threads = nt;
+    h->last_grid = grid;
     return SMAP_OK;
 }
 
@@ -1205,8 +1275,7 @@ smap_status smap_viterbi(smap_handle* h, const float* hist, const float* y_all, 
                                  kind_in(on_device), h->stream));
     st = reset_device_state(h);
     if (st) return st;
-    const int v = h->variant >= 0 ? h->variant : heuristic_variant(h);
-    st = launch_seq(h, v, h->B, 0, h->y, 1, h->order);
+    st = launch_rec(h);
     if (st) return st;
     st = launch_backtrack(h);
     if (st) return st;

@@ -23,6 +23,9 @@ ModelKernels kernels_range_cv() {
     k.dbg[3] = (const void*)debug_svgd_kernel<M, 2, 256, 4>;
     k.dbg[4] = (const void*)debug_svgd_kernel<M, 1, 1024, 1, 8>;
     k.dbg[5] = (const void*)debug_svgd_kernel<M, 1, 1024, 1, 4>;
+    k.rec[0] = (const void*)rec_kernel<M, 2, 512, 1>;
+    k.rec[1] = (const void*)rec_kernel<M, 2, 1024, 1>;
+    k.rec[2] = (const void*)rec_kernel<M, 4, 1024, 1>;
     k.pf[0] = (const void*)pf_seq_kernel<M, 1, 1024>;
     k.pf[1] = (const void*)pf_seq_kernel<M, 4, 1024>;
     return k;

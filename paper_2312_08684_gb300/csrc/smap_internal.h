@@ -23,9 +23,18 @@ constexpr int kNumVariants = 6;
 constexpr VariantInfo kVariants[kNumVariants] = {{1, 1024, 1, 1}, {2, 512, 1, 1}, {4, 256, 1, 1},
                                                  {2, 256, 4, 1}, {1, 1024, 1, 8}, {1, 1024, 1, 4}};
 
+// Compiled variants of the recursion-only kernel (particles per thread, block
+// size bound, minimum resident blocks).
+struct RecVariantInfo {
+    int ppt, maxt, minb;
+};
+constexpr int kNumRecVariants = 3;
+constexpr RecVariantInfo kRecVariants[kNumRecVariants] = {{2, 512, 1}, {2, 1024, 1}, {4, 1024, 1}};
+
 struct ModelKernels {
     int kind, D, DP;
     const void* seq[kNumVariants];   // seq_kernel<M, ...>
+    const void* rec[kNumRecVariants];   // rec_kernel<M, ...>
     const void* dbg[kNumVariants];   // debug_svgd_kernel<M, ...>
     const void* pf[2];               // pf_seq_kernel<M, 1, 1024> (N <= 1024), <M, 4, 1024> (N <= 4096)
 };
@@ -90,6 +99,8 @@ const ModelKernels* kernels_for(int kind);
 bool make_model(int kind, const double* p, int np, ModelParams& mp, std::string& err);
 int variant_threads(int v, int Nmax);
 int pick_variant(int d, int Nmax, int B, int sms);
+int rec_variant_threads(int v, int Nmax);
+int pick_rec_variant(int d, int Nmax);
 __global__ void backtrack_kernel(int B, int Nmax, int maxT, int d, const int* __restrict__ tcur,
                                  const int* __restrict__ Nseq, const double* __restrict__ phi,
                                  const uint16_t* __restrict__ psi, const float* __restrict__ hist,

@@ -35,17 +35,31 @@ struct SmemLayout {
     size_t phis, xs, gs, fs, nrm, phf, cand, zs, red, misc, total;
 };
 
+// The recursion screen takes predecessors in pairs (2q, 2q+1) and in chunks of
+// kRecPairs pairs. Its per-pair arrays are padded after every chunk (16 bytes
+// in the g rows, 8 bytes in the aU pairs), so that lanes rescanning different
+// chunks read different shared-memory banks.
+constexpr int kRecPairs = 16;
+__host__ __device__ inline int rec_pairs(int Np) { return (Np + 1) >> 1; }
+__host__ __device__ inline int rec_chunks(int Np) { return (rec_pairs(Np) + kRecPairs - 1) / kRecPairs; }
+// Offsets in 8-byte units: g row of pair q (DP words), aU word of pair q.
+__host__ __device__ inline int rec_grow(int q, int DP) { return q * DP + 2 * (q / kRecPairs); }
+__host__ __device__ inline int rec_arow(int q) { return q + q / kRecPairs; }
+
 // Dynamic shared memory of the step kernels for Nmax particles of stride DP.
 __host__ __device__ inline SmemLayout smem_layout(int Nmax, int DP) {
     SmemLayout L;
     size_t off = 0;
+    const size_t P = rec_pairs(Nmax), C = rec_chunks(Nmax);
     L.phis = off; off = align16(off + sizeof(double) * Nmax);
     L.xs = off;   off = align16(off + sizeof(float) * Nmax * DP);
-    // gs: SVGD's w rows, or the recursion's aU and 2e arrays (2 Nmax + 4)
+    // gs: SVGD's w rows, or the recursion's aU pairs and 2e array
     const size_t gsf = (size_t)Nmax * (DP < 2 ? 2 : DP);
-    L.gs = off;   off = align16(off + sizeof(float) * (gsf > 2 * (size_t)Nmax + 4 ? gsf : 2 * (size_t)Nmax + 4));
-    // fs: one spare row (the recursion pads an odd predecessor count to a pair)
-    L.fs = off;   off = align16(off + sizeof(float) * (Nmax + 1) * DP);
+    const size_t recf = 2 * (P + C) + 2 * P + 4;
+    L.gs = off;   off = align16(off + sizeof(float) * (gsf > recf ? gsf : recf));
+    // fs: the previous set's rows, or the recursion's g rows in pairs
+    const size_t fsf = (size_t)(Nmax + 1) * DP, gpf = 2 * (P * DP + 2 * C);
+    L.fs = off;   off = align16(off + sizeof(float) * (fsf > gpf ? fsf : gpf));
     L.nrm = off;  off = align16(off + sizeof(float) * Nmax);
     L.phf = off;  off = align16(off + sizeof(float) * Nmax);
     L.cand = off; off = align16(off + sizeof(uint32_t) * kCandCap);
@@ -72,8 +86,26 @@ struct Sm {
     int* ncand;
 };
 
-__device__ inline Sm bind_smem(unsigned char* base, int Nmax, int DP) {
-    const SmemLayout L = smem_layout(Nmax, DP);
+// Dynamic shared memory of the recursion-only kernel: the arrays prepare_step
+// and viterbi_step use (none of the median's or the prior's).
+__host__ __device__ inline SmemLayout rec_smem_layout(int Nmax, int DP) {
+    SmemLayout L;
+    size_t off = 0;
+    const size_t P = rec_pairs(Nmax), C = rec_chunks(Nmax);
+    L.phis = off; off = align16(off + sizeof(double) * Nmax);
+    L.xs = off;   off = align16(off + sizeof(float) * Nmax * DP);
+    L.gs = off;   off = align16(off + sizeof(float) * (2 * (P + C) + 2 * P + 4));
+    const size_t fsf = (size_t)(Nmax + 1) * DP, gpf = 2 * (P * DP + 2 * C);
+    L.fs = off;   off = align16(off + sizeof(float) * (fsf > gpf ? fsf : gpf));
+    L.zs = off;   off = align16(off + sizeof(float) * kMaxDy);
+    L.red = off;  off = align16(off + sizeof(double) * 40);
+    L.misc = off; off = align16(off + sizeof(float) * 64);
+    L.nrm = L.phf = L.cand = off;   // not used by the recursion
+    L.total = off;
+    return L;
+}
+
+__device__ inline Sm bind_smem_at(unsigned char* base, const SmemLayout& L) {
     Sm s;
     s.phis = reinterpret_cast<double*>(base + L.phis);
     s.xs = reinterpret_cast<float*>(base + L.xs);
@@ -89,6 +121,9 @@ __device__ inline Sm bind_smem(unsigned char* base, int Nmax, int DP) {
     s.misc = reinterpret_cast<float*>(base + L.misc);
     s.ncand = reinterpret_cast<int*>(base + L.misc) + 48;
     return s;
+}
+__device__ inline Sm bind_smem(unsigned char* base, int Nmax, int DP) {
+    return bind_smem_at(base, smem_layout(Nmax, DP));
 }
 
 // Row i of a [*][DP] shared array: 128-bit loads when DP is a multiple of 4.
@@ -1092,6 +1127,12 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
     return r;
 }
+// max(a, b, c) in one instruction (a NaN operand is ignored, as by fmaxf).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
 
 // ---------------------------------------------------------------------------
 // a7: forward recursion. The argmax over j of phi_{t-1}(j) + log p(x_i | x^j)
@@ -1128,7 +1169,7 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
 // On return: best[p], phinew[p] for the block's particles. fs is overwritten
 // (g_j replaces f~_j).
 // ---------------------------------------------------------------------------
-template <class M, int PPT>
+template <class M, int PPT, bool kPaired>
 __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, const double* f64,
                              const float* xprev, int* best, double* phinew,
                              unsigned long long* rcnt = nullptr) {
@@ -1143,12 +1184,18 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
     pmax = block_max_d(pmax, s.redd);
     // FP32 magnitudes for the margin of the exact scores: |phi_j| <= |phi~_j| + |max|
     const float mag0 = 2.0f * fabsf((float)pmax) + fabsf(mp.ltc[0]);
-    // per predecessor: aU_j (start of the chain) and 2 e_j, in separate arrays;
-    // g_j = kLam f~_j goes into fs as predecessor pairs (2q, 2q+1) interleaved
-    // per coordinate, [q][c][2], after every row has been read
-    const int Npad = (Np + 1) & ~1;
-    float* aUa = s.gs;
-    float* wa = s.gs + Npad;
+    // Per predecessor: aU_j (start of the chain), 2 e_j and g_j = kLam f~_j
+    // (which replaces f~_j in fs once every row has been read). Two layouts:
+    //   kPaired = false: (aU_j, 2 e_j) pairs in gs, g_j rows [j][DP] in fs;
+    //   kPaired = true:  predecessor pairs (2q, 2q+1) interleaved per
+    //     coordinate, g as [q][c][2] in fs and aU as [q][2] in gs, each with a
+    //     pad after every chunk of kRecPairs pairs; 2 e_j after the aU pairs.
+    const int nq = rec_pairs(Np);
+    float* const aUa = s.gs;
+    float* const wa = kPaired ? s.gs + 2 * (nq + rec_chunks(Np)) : s.gs + 1;
+    auto aidx = [&](int j) { return kPaired ? 2 * rec_arow(j >> 1) + (j & 1) : 2 * j; };
+    auto widx = [&](int j) { return kPaired ? j : 2 * j; };
+    auto gidx = [&](int j, int c) { return kPaired ? 2 * (rec_grow(j >> 1, DP) + c) + (j & 1) : j * DP + c; };
     float gmax2 = 0.0f;
     float gown[PPT][D];
 #pragma unroll
@@ -1170,27 +1217,26 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
         const float half = 0.5f * kLam * F;
         const float H = fabsf(ph) + half;
         const float e = Ke * H + K64 * (fabsf(ph) + mag0 + kLam * F);
-        aUa[j] = (ph - half) + e;
-        wa[j] = 2.0f * e;
+        aUa[aidx(j)] = (ph - half) + e;
+        wa[widx(j)] = 2.0f * e;
+        if constexpr (!kPaired) store_row<D, DP>(s.fs, j, gown[k]);   // the thread's own row
     }
     const float gmax = sqrtf(block_max_f(gmax2, s.redf)) * 1.0000005f;   // its barriers: every fs row read
+    if constexpr (kPaired) {
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int j = tid + k * NT;
-        if (j >= Np) continue;
-        float* gq = s.fs + (size_t)(j >> 1) * 2 * DP + (j & 1);
+        for (int k = 0; k < PPT; ++k) {
+            const int j = tid + k * NT;
+            if (j >= Np) continue;
 #pragma unroll
-        for (int c = 0; c < D; ++c) gq[2 * c] = gown[k][c];
+            for (int c = 0; c < D; ++c) s.fs[gidx(j, c)] = gown[k][c];
+        }
+        if (tid == 0 && (Np & 1)) {   // the pad predecessor: never above any other
+            aUa[aidx(Np)] = -INFINITY;
+#pragma unroll
+            for (int c = 0; c < D; ++c) s.fs[gidx(Np, c)] = 0.0f;
+        }
+        __syncthreads();
     }
-    if (tid == 0 && (Np & 1)) {   // the pad predecessor: never above any other
-        aUa[Np] = -INFINITY;
-        float* gq = s.fs + (size_t)(Np >> 1) * 2 * DP + 1;
-#pragma unroll
-        for (int c = 0; c < D; ++c) gq[2 * c] = 0.0f;
-    }
-    __syncthreads();
-    // g of predecessor j, coordinate c, from the interleaved pairs
-    auto gval = [&](int j, int c) { return s.fs[(size_t)(j >> 1) * 2 * DP + 2 * c + (j & 1)]; };
     float xc[PPT][D], Ei[PPT];
     float cf[D], qk[D];
 #pragma unroll
@@ -1211,65 +1257,151 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
         }
         Ei[p] = Ki * sqrtf(X) * 1.0000005f * gmax + K64 * kLam * X;
     }
-    // One FP32 pass: per particle the largest chain value v1 and the largest
-    // value v2 of every other j (three min/max per pair), and the chunk of 32
-    // predecessors in which v1 was first reached; the chunk is then scanned
-    // again for the first j whose chain value (computed the same way, so
-    // bit-identical) equals v1. The pass takes predecessors in pairs: one
-    // packed FMA advances the chains of j and j + 1 together.
-    constexpr int kChunk = 32;
+    // The FP32 pass: per particle the largest chain value v1, the first j1
+    // reaching it, and the largest value v2 of every other j.
     float v1[PPT], v2[PPT];
     int j1[PPT];
-    unsigned long long xd[PPT][D];
+    if constexpr (!kPaired) {
+        // One chain per predecessor, the running top two (three min/max per
+        // pair), and the chunk of 32 predecessors in which v1 was first
+        // reached; that chunk is then scanned again for the first j whose
+        // chain value (computed the same way, so bit-identical) equals v1.
+        constexpr int kChunk = 32;
+        const float2* ab = reinterpret_cast<const float2*>(aUa);
 #pragma unroll
-    for (int p = 0; p < PPT; ++p) {
-        v1[p] = -INFINITY;
-        v2[p] = -INFINITY;
-        j1[p] = 0;
+        for (int p = 0; p < PPT; ++p) {
+            v1[p] = -INFINITY;
+            v2[p] = -INFINITY;
+            j1[p] = 0;
+        }
+        for (int j0 = 0; j0 < Np; j0 += kChunk) {
+            float vb[PPT];
 #pragma unroll
-        for (int c = 0; c < D; ++c) xd[p][c] = pk2(xc[p][c], xc[p][c]);
-    }
-    const unsigned long long* g2 = reinterpret_cast<const unsigned long long*>(s.fs);
-    const unsigned long long* a2 = reinterpret_cast<const unsigned long long*>(aUa);
-    for (int q0 = 0; q0 < Npad / 2; q0 += kChunk / 2) {
-        float vb[PPT];
+            for (int p = 0; p < PPT; ++p) vb[p] = v1[p];
+            const int je = min(j0 + kChunk, Np);
+            for (int j = j0; j < je; ++j) {
+                float gj[D];
+                load_row<D, DP>(s.fs, j, gj);
+                const float aU = ab[j].x;
 #pragma unroll
-        for (int p = 0; p < PPT; ++p) vb[p] = v1[p];
-        const int qe = min(q0 + kChunk / 2, Npad / 2);
-        for (int q = q0; q < qe; ++q) {
-            unsigned long long gp[D];
+                for (int p = 0; p < PPT; ++p) {
+                    float v = aU;
 #pragma unroll
-            for (int c = 0; c < D; ++c) gp[c] = g2[(size_t)q * DP + c];
-            const unsigned long long aU = a2[q];
+                    for (int c = 0; c < D; ++c) v = fmaf(xc[p][c], gj[c], v);
+                    const float lo = fminf(v1[p], v);
+                    v1[p] = fmaxf(v1[p], v);
+                    v2[p] = fmaxf(v2[p], lo);
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < PPT; ++p) j1[p] = v1[p] > vb[p] ? j0 : j1[p];
+        }
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            const int j0 = j1[p], je = min(j0 + kChunk, Np);
+            for (int j = j0; j < je; ++j) {
+                float gj[D];
+                load_row<D, DP>(s.fs, j, gj);
+                float v = ab[j].x;
+#pragma unroll
+                for (int c = 0; c < D; ++c) v = fmaf(xc[p][c], gj[c], v);
+                if (v == v1[p]) {
+                    j1[p] = j;
+                    break;
+                }
+            }
+        }
+    } else {
+        // Predecessor pairs: one packed FMA advances the chains of j and j + 1
+        // together, and a three-input max keeps the largest chain value of the
+        // chunk (kRecPairs pairs). Over the chunks each particle keeps the
+        // largest value (v1), the first chunk reaching it, and the largest
+        // value c2 of every other chunk. The chunk of v1 is then scanned again
+        // (the same packed chains, so bit-identical values) for the first j
+        // whose value equals v1 and the largest value of its other members.
+        float c2[PPT];
+        unsigned long long xd[PPT][D];
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            v1[p] = -INFINITY;
+            c2[p] = -INFINITY;
+            j1[p] = 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) xd[p][c] = pk2(xc[p][c], xc[p][c]);
+        }
+        const unsigned long long* g2 = reinterpret_cast<const unsigned long long*>(s.fs);
+        const unsigned long long* a2 = reinterpret_cast<const unsigned long long*>(aUa);
+        // the g row of pair q of a chunk (DP words, 16-byte aligned when DP is even)
+        auto load_g = [&](const unsigned long long* gq, unsigned long long* gp) {
+            if constexpr (DP % 2 == 0) {
+#pragma unroll
+                for (int c = 0; c < D; c += 2) {
+                    const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(gq + c);
+                    gp[c] = w.x;
+                    if (c + 1 < D) gp[c + 1] = w.y;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < D; ++c) gp[c] = gq[c];
+            }
+        };
+        for (int q0 = 0; q0 < nq; q0 += kRecPairs) {
+            const unsigned long long* gq = g2 + rec_grow(q0, DP);
+            const unsigned long long* aq = a2 + rec_arow(q0);
+            float cm[PPT];
+#pragma unroll
+            for (int p = 0; p < PPT; ++p) cm[p] = -INFINITY;
+            auto pair_step = [&](int t) {
+                unsigned long long gp[D];
+                load_g(gq + t * DP, gp);
+                const unsigned long long aU = aq[t];
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) {
+                    unsigned long long v = aU;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) v = ffma2(xd[p][c], gp[c], v);
+                    float va, vz;
+                    upk2(v, va, vz);
+                    cm[p] = fmax3(cm[p], va, vz);
+                }
+            };
+            const int n = min(kRecPairs, nq - q0);
+            if (n == kRecPairs) {
+#pragma unroll 4
+                for (int t = 0; t < kRecPairs; ++t) pair_step(t);
+            } else {
+                for (int t = 0; t < n; ++t) pair_step(t);
+            }
 #pragma unroll
             for (int p = 0; p < PPT; ++p) {
-                unsigned long long v = aU;
+                const float lo = fminf(v1[p], cm[p]);
+                j1[p] = cm[p] > v1[p] ? q0 : j1[p];
+                v1[p] = fmaxf(v1[p], cm[p]);
+                c2[p] = fmaxf(c2[p], lo);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            const int q0 = j1[p], n = min(kRecPairs, nq - q0);
+            const unsigned long long* gq = g2 + rec_grow(q0, DP);
+            const unsigned long long* aq = a2 + rec_arow(q0);
+            float s2 = -INFINITY;
+            int jj = -1;
+            for (int t = 0; t < n; ++t) {
+                unsigned long long gp[D];
+                load_g(gq + t * DP, gp);
+                unsigned long long v = aq[t];
 #pragma unroll
                 for (int c = 0; c < D; ++c) v = ffma2(xd[p][c], gp[c], v);
                 float va, vz;
                 upk2(v, va, vz);
-                float lo = fminf(v1[p], va);
-                v1[p] = fmaxf(v1[p], va);
-                v2[p] = fmaxf(v2[p], lo);
-                lo = fminf(v1[p], vz);
-                v1[p] = fmaxf(v1[p], vz);
-                v2[p] = fmaxf(v2[p], lo);
+                if (jj < 0 && va == v1[p]) jj = 2 * (q0 + t);
+                else s2 = fmaxf(s2, va);
+                if (jj < 0 && vz == v1[p]) jj = 2 * (q0 + t) + 1;
+                else s2 = fmaxf(s2, vz);
             }
-        }
-#pragma unroll
-        for (int p = 0; p < PPT; ++p) j1[p] = v1[p] > vb[p] ? 2 * q0 : j1[p];
-    }
-#pragma unroll
-    for (int p = 0; p < PPT; ++p) {
-        const int j0 = j1[p], je = min(j0 + kChunk, Np);
-        for (int j = j0; j < je; ++j) {
-            float v = aUa[j];
-#pragma unroll
-            for (int c = 0; c < D; ++c) v = fmaf(xc[p][c], gval(j, c), v);
-            if (v == v1[p]) {
-                j1[p] = j;
-                break;
-            }
+            j1[p] = jj < 0 ? 2 * q0 : jj;
+            v2[p] = fmaxf(c2[p], s2);
         }
     }
     // candidate threshold: v_ij >= v1 - 2 e_j1 - 2 E_i can still be the maximum
@@ -1277,7 +1409,7 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
     bool uniq[PPT];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
-        const float m = (wa[j1[p]] + 2.0f * Ei[p]) * 1.0000005f;
+        const float m = (wa[widx(j1[p])] + 2.0f * Ei[p]) * 1.0000005f;
         uniq[p] = (v1[p] - v2[p]) > m;
         thr[p] = v1[p] - m;
     }
@@ -1329,9 +1461,9 @@ __device__ void viterbi_step(const ModelParams& mp, const Sm& s, int N, int Np, 
                 double bsv = -INFINITY, blv = 0.0;
                 int bj = 0x7fffffff;
                 for (int j = lane; j < Np; j += 32) {
-                    float v = aUa[j];
+                    float v = aUa[aidx(j)];
 #pragma unroll
-                    for (int c = 0; c < D; ++c) v = fmaf(xb[c], gval(j, c), v);
+                    for (int c = 0; c < D; ++c) v = fmaf(xb[c], s.fs[gidx(j, c)], v);
                     if (v >= tb) {
                         const double lt = logtrans(rb, j);
                         if (rcnt) atomicAdd(&rcnt[2], 1ull);
@@ -1467,7 +1599,7 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
             double phinew[PPT];
             if (!SMAP_DBG(t >= 1 && t <= a.maxT, kDbgStep, t)) break;
             const float* xprev = (t >= 2) ? a.hist + (((size_t)b * a.maxT + (t - 2)) * a.Nmax) * D : nullptr;
-            viterbi_step<M, PPT>(mp, s, N, Np, f64, xprev, best, phinew, s_rcnt);
+            viterbi_step<M, PPT, false>(mp, s, N, Np, f64, xprev, best, phinew, s_rcnt);
             __syncthreads();   // all reads of phis / xs done
             bool bad = false;
             float* dst = a.hist + (((size_t)b * a.maxT + (t - 1)) * a.Nmax) * D;
@@ -1501,6 +1633,83 @@ __global__ void __launch_bounds__(MAXT, MINB) seq_kernel(const __grid_constant__
         if (tid == 0) {
             a.tcur[b] = tdone;
             a.bwguess[b] = st.have ? st.med : 0.0f;
+        }
+    }
+    __syncthreads();
+    if (a.rstats && tid < 3 && s_rcnt[tid]) atomicAdd(&a.rstats[tid], s_rcnt[tid]);
+}
+
+// ---------------------------------------------------------------------------
+// The forward recursion and its stores alone, on given particle sets (hist
+// holds x_t of every step): persistent CTAs over the same work queue as the
+// step kernel, the previous set resident in shared memory, the screen of
+// viterbi_step in its paired form. On return phi, psi, tcur of every
+// sequence are those of the whole sequence (status 6 where a score is not
+// finite), exactly as the step kernel's recursion-only mode leaves them.
+// ---------------------------------------------------------------------------
+template <class M, int PPT, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) rec_kernel(const __grid_constant__ SeqArgs a) {
+    constexpr int D = M::D;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Sm s = bind_smem_at(smem_raw, rec_smem_layout(a.Nmax, M::DP));
+    SMAP_DBG_BEGIN(a.Nmax, a.stats ? a.stats + kDbgWord : nullptr);
+    const ModelParams& mp = a.mp;
+    const int tid = threadIdx.x, NT = blockDim.x;
+    __shared__ int s_item;
+    double* f64 = a.f64 + (size_t)blockIdx.x * a.Nmax * D;
+    __shared__ unsigned long long s_rcnt[3];
+    if (tid < 3) s_rcnt[tid] = 0ull;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= a.B) break;
+        const int b = a.order ? a.order[item] : a.seq_base + item;
+        if (!SMAP_DBG(b >= 0 && b < a.Btot, kDbgSeq, b)) continue;
+        if (a.status[b] != 0) continue;
+        const int N = a.Nseq[b], T = a.Tend[b];
+        if (T > a.maxT || N < 1 || N > a.Nmax) {
+            if (tid == 0) a.status[b] = 1;
+            continue;
+        }
+        if (tid == 0) s.phis[0] = 0.0;
+        int Np = 1, tdone = 0;
+        __syncthreads();
+        for (int t = 1; t <= T; ++t) {
+            if (!SMAP_DBG(t <= a.maxT, kDbgStep, t)) break;
+            const size_t row = (size_t)b * a.maxT + (t - 1);
+            const float* xt = a.hist + row * a.Nmax * D;
+            prepare_step<M, PPT>(mp, s, t, N, Np, t == 1, a.x0 + (size_t)b * D, a.y + row * mp.dy, f64, 0,
+                                 a.seed, (uint32_t)b, xt, t >= 2);
+            int best[PPT];
+            double phinew[PPT];
+            const float* xprev = (t >= 2) ? xt - (size_t)a.Nmax * D : nullptr;
+            viterbi_step<M, PPT, true>(mp, s, N, Np, f64, xprev, best, phinew, s_rcnt);
+            __syncthreads();   // all reads of phis / xs done
+            bool bad = false;
+            uint16_t* pdst = a.psi + row * a.Nmax;
+#pragma unroll
+            for (int p = 0; p < PPT; ++p) {
+                const int i = tid + p * NT;
+                if (i >= N) continue;
+                s.phis[i] = phinew[p];
+                bad |= !isfinite(phinew[p]);
+                pdst[i] = (uint16_t)best[p];
+            }
+            bad = __syncthreads_or(bad);
+            if (bad) {
+                if (tid == 0) a.status[b] = 6;   // SMAP_E_NONFINITE
+                break;
+            }
+            tdone = t;
+            Np = N;
+        }
+        __syncthreads();
+        for (int j = tid; j < N; j += NT) a.phi[(size_t)b * a.Nmax + j] = s.phis[j];
+        if (tid == 0) {
+            a.tcur[b] = tdone;
+            a.bwguess[b] = 0.0f;
         }
     }
     __syncthreads();

@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(MAXT, 1) pf_seq_kernel(const __grid_constant__
                                     (uint32_t)b);
             int best[PPT];
             double phinew[PPT];
-            viterbi_step<M, PPT>(mp, s, N, Np, f64, nullptr, best, phinew);   // FP64 states: FP64 terms
+            viterbi_step<M, PPT, true>(mp, s, N, Np, f64, nullptr, best, phinew);   // FP64 states: FP64 terms
             __syncthreads();   // all reads of phis / xs done
             bool bad = false;
             float* dst = a.hist + (((size_t)b * a.maxT + (t - 1)) * a.Nmax) * D;
