@@ -337,20 +337,11 @@ __device__ inline void bitonic_sort(uint32_t* c, int n2) {
 template <int D, int DP>
 __device__ bool bracket_pass(const Sm& s, int N, float lo, float hi, int r1, int r2, uint32_t& v1,
                              uint32_t& v2, int& nc_out) {
-    // the keys below lo: per-warp sums added into a shared counter, so that
-    // one barrier publishes both counts and the collected candidates
-    int* nlo_sum = s.ncand + 1;
-    if (threadIdx.x == 0) {
-        *s.ncand = 0;
-        *nlo_sum = 0;
-    }
+    if (threadIdx.x == 0) *s.ncand = 0;
     __syncthreads();
     BracketCount f{lo, hi, 0, s.cand, s.ncand};
     for_each_pair<D, DP>(s.xs, s.nrm, N, f);
-    const int wsum = warp_sum_int(f.nlo);
-    if (lane_id() == 0 && wsum) atomicAdd(nlo_sum, wsum);
-    __syncthreads();
-    const int nlo = *nlo_sum;
+    const int nlo = block_sum_int(f.nlo, s.redi);   // ends with a barrier
     const int nc = *s.ncand;
     nc_out = nc;
     const bool inside = nlo <= r1 && r2 < nlo + nc;
